@@ -1,0 +1,214 @@
+/*
+ * gmine.h -- C ABI of libgmine, the GB300 (sm_103a) implementation of the
+ * MINE statistics over many variable pairs.
+ *
+ * The calls follow the problem statement of the C engine the paper describes
+ * (Sec. "The MINE C engine and its wrappers"): a dataset of variables, a
+ * parameter structure {alpha, c}, and per pair a score structure holding the
+ * characteristic matrix M and the four statistics MIC, MAS, MEV, MCN.
+ *
+ * Definitions implemented (the method's steps, in the order the paper and the
+ * SOM algorithms it refers to give them):
+ *   B = floor(n^alpha) with n the samples left after dropping missing ones
+ *     (Sec. 2C: B(n) = n^alpha);
+ *   for both orientations and every row count y = 2..floor(B/2):
+ *     EquipartitionYAxis of the row variable (Appendix items 3-4),
+ *     GetClumpsPartition / GetSuperclumpsPartition of the column variable
+ *     with khat = floor(c * floor(B/y)) (Appendix items 5-7, the two
+ *     algorithm listings), and the OptimizeXAxis dynamic program over the
+ *     superclumps with precomputed cell counts and entropy terms (Appendix
+ *     item 10), giving I(x, y) for x = 2..floor(B/y);
+ *   M(x,y) = I / log min(x, yhat), the larger of the two orientations,
+ *     over x*y <= B (Appendix items 1 and 4);
+ *   MIC = max M; MAS = max |M(x,y) - M(y,x)|; MEV = max M over x = 2 or
+ *     y = 2; MCN = min log2(xy) over the cells with M = MIC (Appendix item 2).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are CUDA device pointers, h_* host pointers.  The
+ *     caller owns every buffer; the library keeps no pointer after a call
+ *     returns.  Except for gmine_score_pair_host, no call allocates device
+ *     memory: gmine_plan reports the workspace the caller must provide.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls taking d_* pointers only enqueue work on it and
+ *     return; results are ready once the stream has been synchronised.
+ *   - Every call returns an int status (GMINE_OK = 0 or a GMINE_E_* code);
+ *     nothing aborts or throws across this boundary.  A per-pair status is
+ *     also stored in each gmine_pair_score.
+ *   - Variables are stored variable-major: d_vars[v * n + i] is sample i of
+ *     variable v (one variable per row, as in the paper's data files).  A
+ *     sample that is NaN or infinite is missing; a pair uses the samples
+ *     where both of its variables are finite.
+ *   - Pairs are int32 [n_pairs][2]: (index of X, index of Y).  In the score
+ *     of a pair, M(x, y) has x columns on X and y rows on Y.
+ */
+#ifndef GMINE_H
+#define GMINE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMINE_ABI_VERSION 1
+
+/* status codes */
+#define GMINE_OK 0
+#define GMINE_E_PARAM 1      /* alpha not in (0, 1] or c not finite and > 0 */
+#define GMINE_E_TOO_FEW 2    /* pair: fewer than 4 usable samples or B < 4 */
+#define GMINE_E_CONSTANT 3   /* pair: a variable is constant on the used
+                                samples; that orientation contributes M = 0 */
+#define GMINE_E_NOMEM 4      /* host or device allocation failed */
+#define GMINE_E_ARG 5        /* NULL pointer, negative size, bad index */
+#define GMINE_E_WORKSPACE 6  /* workspace smaller than gmine_plan reported */
+#define GMINE_E_CUDA 7       /* a CUDA runtime call failed */
+#define GMINE_E_LIMIT 8      /* a size beyond what this build supports */
+#define GMINE_E_NODEVICE 9   /* no usable CUDA device */
+
+/* precision of the OptimizeXAxis dynamic program */
+#define GMINE_PLAIN_FP64 0            /* entropies and DP in double */
+#define GMINE_FP32_DP_FP64_RESCORE 1  /* DP in float with exact int32 counts;
+                                         each chosen partition re-scored in
+                                         double */
+
+/* Parameters (Sec. "The MINE C engine": the configuration structure).
+   alpha: B = n^alpha, 0 < alpha <= 1 (paper default 0.6);
+   c: clump factor, khat = c * x, c > 0 (paper default 15). */
+typedef struct {
+    double alpha;
+    double c;
+} gmine_param;
+
+/* Score of one pair (72 bytes). */
+typedef struct {
+    double mic, mas, mev, mcn;
+    int64_t m_offset;   /* first cell of this pair in d_M / h_M           */
+    int32_t n_used;     /* samples where both variables are finite        */
+    int32_t B;          /* floor(n_used^alpha)                            */
+    int32_t m_cells;    /* cells (x, y), x, y >= 2, x*y <= B, y-major     */
+    int32_t mcn_xy;     /* the x*y whose log2 is MCN                      */
+    int32_t status;     /* GMINE_OK, GMINE_E_TOO_FEW or GMINE_E_CONSTANT  */
+    int32_t yhat_x;     /* rows used when X is equipartitioned into 2     */
+    int32_t yhat_y;     /* rows used when Y is equipartitioned into 2     */
+    int32_t reserved;
+} gmine_pair_score;
+
+/* Optional per-task outputs of gmine_compute_batch_ex, for parity checks of
+   the integer quantities.  A task is (pair, orientation o, row count y):
+   o = 0 equipartitions Y and optimises columns on X, o = 1 the reverse.
+   Task t of the batch is  t = ((y - 2) * 2 + o) * n_pairs + pair  for
+   y = 2 .. floor(B_max/2), B_max = floor(n^alpha) of the full sample count.
+   Every pointer may be NULL.  Strides are in elements. */
+typedef struct {
+    int32_t *d_k;         /* [tasks] superclumps k (0 if task is empty)    */
+    int32_t *d_yhat;      /* [tasks] rows used                              */
+    int32_t *d_clumps;    /* [tasks] clumps before the superclump step      */
+    int32_t *d_sc_ends;   /* [tasks][sc_stride] superclump ends c_0..c_k    */
+    int32_t sc_stride;
+    int32_t cut_stride;
+    int32_t *d_cuts;      /* [tasks][cut_stride] chosen partition of each
+                             l = 2..x: its l-1 column ends (superclump
+                             indices) packed at (l-2)(l-1)/2; -1 where l > k */
+    double *d_I;          /* [tasks][I_stride] I(l) for l = 2..x            */
+    int32_t I_stride;
+    int32_t reserved;
+} gmine_trace;
+
+/* ---- parameters, errors ------------------------------------------------ */
+
+int gmine_abi_version(void);
+
+/* GMINE_OK if 0 < alpha <= 1 and c is finite and > 0, else GMINE_E_PARAM
+   (the C++ wrapper of the paper rejects invalid parameters). */
+int gmine_check_param(const gmine_param *param);
+
+/* Static English text for a status code. */
+const char *gmine_strerror(int status);
+
+/* B = floor(n^alpha) as the library computes it (double pow on the host). */
+int gmine_B(int64_t n, double alpha);
+
+/* Number of cells of M for a given B. */
+int64_t gmine_m_cells(int32_t B);
+
+/* ---- batch over pairs -------------------------------------------------- */
+
+/* flags for gmine_plan */
+#define GMINE_PLAN_HOST_STAGING 1   /* workspace also holds device copies of
+                                       the inputs and outputs, as needed by
+                                       gmine_compute_batch_host */
+#define GMINE_PLAN_TRACE 2          /* room for gmine_trace scratch tables */
+
+/* Sizes for a batch of n_pairs pairs over p variables of n samples.
+   *m_cells_per_pair: cells of M reserved per pair (pair i's cells start at
+   i * m_cells_per_pair in d_M).  *workspace_bytes: device workspace to pass
+   to the compute calls (256-byte aligned).  Either output may be NULL. */
+int gmine_plan(int64_t p, int64_t n, int64_t n_pairs, const gmine_param *param,
+               int32_t precision, int32_t flags, int64_t *m_cells_per_pair,
+               int64_t *workspace_bytes);
+
+/* The characteristic matrix and statistics of every pair (the paper's
+   mine_compute_score over a dataset).  d_vars [p][n] double, d_pairs
+   [n_pairs][2] int32, d_scores [n_pairs], d_M [n_pairs * m_cells_per_pair]
+   double or NULL.  Asynchronous on `stream`. */
+int gmine_compute_batch(const double *d_vars, int64_t p, int64_t n,
+                        const int32_t *d_pairs, int64_t n_pairs,
+                        const gmine_param *param, int32_t precision,
+                        void *d_workspace, int64_t workspace_bytes,
+                        gmine_pair_score *d_scores, double *d_M, void *stream);
+
+/* As gmine_compute_batch, plus the per-task outputs of `trace` (may be
+   NULL; the workspace must then be planned with GMINE_PLAN_TRACE). */
+int gmine_compute_batch_ex(const double *d_vars, int64_t p, int64_t n,
+                           const int32_t *d_pairs, int64_t n_pairs,
+                           const gmine_param *param, int32_t precision,
+                           void *d_workspace, int64_t workspace_bytes,
+                           gmine_pair_score *d_scores, double *d_M,
+                           const gmine_trace *trace, void *stream);
+
+/* Host buffers in and out: copies h_vars and h_pairs into the workspace
+   (planned with GMINE_PLAN_HOST_STAGING), computes, copies the scores (and M
+   if h_M is not NULL) back and synchronises `stream` before returning. */
+int gmine_compute_batch_host(const double *h_vars, int64_t p, int64_t n,
+                             const int32_t *h_pairs, int64_t n_pairs,
+                             const gmine_param *param, int32_t precision,
+                             void *d_workspace, int64_t workspace_bytes,
+                             gmine_pair_score *h_scores, double *h_M,
+                             void *stream);
+
+/* ---- single steps, the same kernels as the batch uses ------------------ */
+
+/* Tie-aware sort of every variable (finite samples; no NaN allowed):
+   d_perm[v][m] = sample at sorted position m (ties by sample index),
+   d_rank[v][i] = dense rank of sample i (0 = smallest value),
+   d_groups[v] = number of distinct values.  Workspace as gmine_plan(p, n,
+   0, ...) reports.  GMINE_E_ARG if a variable holds a non-finite sample. */
+int gmine_rank(const double *d_vars, int64_t p, int64_t n, int32_t *d_perm,
+               int32_t *d_rank, int32_t *d_groups, void *d_workspace,
+               int64_t workspace_bytes, void *stream);
+
+/* EquipartitionYAxis (SOM Alg. 3; Appendix items 3-4) of every variable
+   into y rows: d_Q[v][i] = 0-based row of sample i, d_yhat[v] = rows used. */
+int gmine_equipartition(const double *d_vars, int64_t p, int64_t n, int32_t y,
+                        int32_t *d_Q, int32_t *d_yhat, void *d_workspace,
+                        int64_t workspace_bytes, void *stream);
+
+/* ---- one pair, host memory (convenience; allocates and synchronises) --- */
+
+/* mine_compute_score for one dataset of two variables x, y of n samples.
+   M_out may be NULL, else it receives out->m_cells doubles. */
+int gmine_score_pair_host(const double *h_x, const double *h_y, int64_t n,
+                          const gmine_param *param, int32_t precision,
+                          gmine_pair_score *out, double *M_out);
+
+/* The four statistic functions of the paper's score structure. */
+double gmine_mic(const gmine_pair_score *s);
+double gmine_mas(const gmine_pair_score *s);
+double gmine_mev(const gmine_pair_score *s);
+double gmine_mcn(const gmine_pair_score *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMINE_H */

@@ -1,0 +1,563 @@
+// gmine_api.cu -- host side of the libgmine C ABI (include/gmine.h):
+// parameter checks, workspace planning, and the launch sequence of a batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gmine.h"
+#include "gmine_internal.cuh"
+#include "kernels.h"
+
+using namespace gm;
+
+namespace {
+
+constexpr int kTaskThreads = 256;
+constexpr int64_t kChunkPairs = 32768;
+constexpr int kRankThreads = 1024;
+
+int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
+int align16i(int64_t b) { return (int)((b + 15) & ~int64_t(15)); }
+
+#define GM_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      last_cuda_error() = e_;                                  \
+      return GMINE_E_CUDA;                                     \
+    }                                                          \
+  } while (0)
+
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+int host_B(int64_t n, double alpha) { return (int)std::floor(std::pow((double)n, alpha)); }
+
+int host_khat(int B, int y, double c) {
+  const int x = B / y;
+  const int k = (int)std::floor(c * (double)x);
+  return k < 1 ? 1 : k;
+}
+
+int64_t host_cells(int B) {
+  int64_t cells = 0;
+  for (int y = 2; y <= B / 2; ++y) cells += B / y - 1;
+  return cells;
+}
+
+struct DeviceInfo {
+  int sms = 0;
+  int smem_optin = 0;
+};
+
+int device_info(DeviceInfo* d) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GMINE_E_NODEVICE;
+  if (cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return GMINE_E_NODEVICE;
+  if (cudaDeviceGetAttribute(&d->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return GMINE_E_NODEVICE;
+  return GMINE_OK;
+}
+
+// Shape bounds of the tasks of a batch with n samples and parameters (B, c).
+struct TaskBounds {
+  int B, R, xmax, kmax, cum_max;
+  int64_t welems;
+};
+
+TaskBounds task_bounds(int n, int B, double c) {
+  TaskBounds tb{};
+  tb.B = B;
+  tb.R = std::max(B / 2 - 1, 0);
+  tb.xmax = B / 2;
+  for (int y = 2; y <= B / 2; ++y) {
+    const int kk = std::min(host_khat(B, y, c), n);
+    const int x = B / y;
+    tb.kmax = std::max(tb.kmax, kk);
+    tb.cum_max = std::max(tb.cum_max, y * (kk + 1));
+    tb.welems = std::max(tb.welems, (int64_t)(std::min(x, kk) + 1) * (kk + 1));
+  }
+  return tb;
+}
+
+SmemPlan make_plan(int n, const TaskBounds& tb, bool fp32, bool trace, int smem_optin,
+                   bool* w_in_smem) {
+  SmemPlan S{};
+  const int rs = fp32 ? 4 : 8;
+  int o = 0;
+  S.offP_Qs = o; o = align16i(o + 2LL * n);
+  S.offP_q = o; o = align16i(o + 2LL * n);
+  S.offP_mixed = o; o = align16i(o + (int64_t)n);
+  S.offP_cflag = o; o = align16i(o + (int64_t)n);
+  S.offP_grpU = o; o = align16i(o + 4LL * n);
+  S.offP_cgrp = o; o = align16i(o + 4LL * n);
+  S.offP_cstart = o; o = align16i(o + 4LL * (n + 1));
+  S.sizeP = o;
+  int k = 0;
+  const int keb = k; k = align16i(k + 4LL * (tb.B / 2 + 2));
+  const int kscb = k; k = align16i(k + 4LL * (tb.kmax + 1));
+  const int kcum = k; k = align16i(k + 4LL * std::max(tb.cum_max, 1));
+  const int kE = k; k = align16i(k + (int64_t)rs * (tb.kmax + 1));
+  const int kV = k; k = align16i(k + (int64_t)rs * (tb.xmax + 1));
+  const int kVa = k; k = align16i(k + 4LL * (tb.xmax + 1));
+  const int ktmp = k; k = align16i(k + 4LL * (kTaskThreads + 1));
+  const int sizeK = k;
+  // DP tables: W (real) and, for the float path, the int16 argmax table
+  int64_t wbytes = ((tb.welems * rs + 15) & ~15LL);
+  if (fp32) wbytes += ((tb.welems * 2 + 15) & ~15LL);
+  const int reserve = 1024;  // static shared memory of the kernel
+  // prefer both regions in shared memory, then the DP tables alone, then
+  // the prologue alone, then neither (per-CTA global scratch instead)
+  bool p_smem, w_smem;
+  if (std::max<int64_t>(S.sizeP, wbytes) + sizeK + reserve <= smem_optin) {
+    p_smem = true; w_smem = true;
+  } else if (wbytes + sizeK + reserve <= smem_optin) {
+    p_smem = false; w_smem = true;
+  } else if ((int64_t)S.sizeP + sizeK + reserve <= smem_optin) {
+    p_smem = true; w_smem = false;
+  } else {
+    p_smem = false; w_smem = false;
+  }
+  *w_in_smem = w_smem;
+  S.p_in_smem = p_smem ? 1 : 0;
+  S.w_bytes = w_smem ? (int)wbytes : 0;
+  const int offK = align16i(std::max<int64_t>(p_smem ? S.sizeP : 0, S.w_bytes));
+  S.offK_eb = offK + keb;
+  S.offK_scb = offK + kscb;
+  S.offK_cum = offK + kcum;
+  S.offK_Ecol = offK + kE;
+  S.offK_V = offK + kV;
+  S.offK_Varg = offK + kVa;
+  S.offK_tmp = offK + ktmp;
+  S.total = offK + sizeK;
+  S.scratch_P = p_smem ? 0 : align256(S.sizeP);
+  S.scratch_tables = w_smem ? 0 : (int64_t)align256(wbytes);
+  S.scratch_A32 = (!fp32 && trace) ? align256(tb.welems * 4) : 0;
+  S.scratch_cuts = align256((int64_t)tb.xmax * std::max(tb.xmax - 1, 1) / 2 * 4 + 4);
+  S.scratch_total = S.scratch_P + S.scratch_tables + S.scratch_A32 + S.scratch_cuts;
+  return S;
+}
+
+// Workspace layout of a batch (byte offsets from the workspace base).
+struct Layout {
+  int64_t n, p, n_pairs, chunk, slots;
+  int B;
+  TaskBounds tb;
+  SmemPlan S;
+  bool w_in_smem;
+  int task_ctas;
+  int64_t cells_max;
+  int64_t o_Btab, o_L64, o_L32, o_lnt, o_nf;
+  int64_t o_perm, o_pos, o_grp, o_gstart, o_ngroups, o_nslot;
+  int64_t o_bounds, o_yhat;
+  int64_t o_slot, o_nused, o_Bp, o_flags, o_dirty, o_ndirty;
+  int64_t o_Mo, o_queue, o_scratch;
+  int64_t o_hvars, o_hpairs, o_hscores, o_hM;
+  int64_t total;
+};
+
+int task_occupancy(bool fp32, int smem, int* blocks) {
+  const cudaError_t e = task_configure(fp32, smem, kTaskThreads, blocks);
+  if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+  return GMINE_OK;
+}
+
+int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
+                int32_t flags, Layout* L) {
+  if (!param) return GMINE_E_ARG;
+  if (gmine_check_param(param) != GMINE_OK) return GMINE_E_PARAM;
+  if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
+  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
+  if (n > kMaxRankN) return GMINE_E_LIMIT;
+  DeviceInfo dev;
+  int rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  *L = Layout{};
+  L->n = n;
+  L->p = p;
+  L->n_pairs = n_pairs;
+  L->chunk = std::max<int64_t>(1, std::min<int64_t>(n_pairs, kChunkPairs));
+  L->slots = p + 2 * L->chunk;
+  L->B = n > 0 ? host_B(n, param->alpha) : 0;
+  L->tb = task_bounds((int)n, L->B, param->c);
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  const bool trace = (flags & GMINE_PLAN_TRACE) != 0;
+  L->S = make_plan((int)n, L->tb, fp32, trace, dev.smem_optin, &L->w_in_smem);
+  if (L->S.total > dev.smem_optin) return GMINE_E_LIMIT;
+  int blocks = 0;
+  rc = task_occupancy(fp32, L->S.total, &blocks);
+  if (rc != GMINE_OK) return rc;
+  if (blocks < 1) return GMINE_E_LIMIT;
+  L->task_ctas = blocks * dev.sms;
+  L->cells_max = std::max<int64_t>(host_cells(L->B), 1);
+
+  const int64_t S = L->slots;
+  const int R = std::max(L->tb.R, 1);
+  const int bstride = L->tb.R + 2;
+  int64_t o = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t at = o;
+    o = align256(o + std::max<int64_t>(bytes, 1));
+    return at;
+  };
+  L->o_Btab = take(4 * (n + 1));
+  L->o_L64 = take(8 * (n + 1));
+  L->o_L32 = take(4 * (n + 1));
+  L->o_lnt = take(8 * (n + 1));
+  L->o_nf = take(4 * p);
+  L->o_perm = take(4 * S * n);
+  L->o_pos = take(4 * S * n);
+  L->o_grp = take(4 * S * n);
+  L->o_gstart = take(4 * S * (n + 1));
+  L->o_ngroups = take(4 * S);
+  L->o_nslot = take(4 * S);
+  L->o_bounds = take(4 * S * (int64_t)R * bstride);
+  L->o_yhat = take(4 * S * (int64_t)R);
+  L->o_slot = take(4 * 2 * L->chunk);
+  L->o_nused = take(4 * L->chunk);
+  L->o_Bp = take(4 * L->chunk);
+  L->o_flags = take(4 * L->chunk);
+  L->o_dirty = take(4 * L->chunk);
+  L->o_ndirty = take(4);
+  L->o_Mo = take(8 * L->chunk * 2 * L->cells_max);
+  L->o_queue = take(8);
+  L->o_scratch = take(L->S.scratch_total * L->task_ctas);
+  if (flags & GMINE_PLAN_HOST_STAGING) {
+    L->o_hvars = take(8 * p * n);
+    L->o_hpairs = take(4 * 2 * n_pairs);
+    L->o_hscores = take((int64_t)sizeof(gmine_pair_score) * n_pairs);
+    L->o_hM = take(8 * n_pairs * L->cells_max);
+  } else {
+    L->o_hvars = L->o_hpairs = L->o_hscores = L->o_hM = -1;
+  }
+  L->total = o;
+  return GMINE_OK;
+}
+
+template <typename T>
+T* at(void* base, int64_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+RankData rank_data(void* ws, const Layout& L) {
+  RankData rk;
+  rk.perm = at<int32_t>(ws, L.o_perm);
+  rk.pos = at<int32_t>(ws, L.o_pos);
+  rk.grp = at<int32_t>(ws, L.o_grp);
+  rk.gstart = at<int32_t>(ws, L.o_gstart);
+  rk.ngroups = at<int32_t>(ws, L.o_ngroups);
+  rk.nslot = at<int32_t>(ws, L.o_nslot);
+  rk.stride = L.n;
+  return rk;
+}
+
+EquiData equi_data(void* ws, const Layout& L) {
+  EquiData eq;
+  eq.bounds = at<int32_t>(ws, L.o_bounds);
+  eq.yhat = at<int32_t>(ws, L.o_yhat);
+  eq.R = std::max(L.tb.R, 1);
+  eq.bstride = L.tb.R + 2;
+  return eq;
+}
+
+PairPrep pair_prep(void* ws, const Layout& L) {
+  PairPrep pp;
+  pp.slot = at<int32_t>(ws, L.o_slot);
+  pp.n_used = at<int32_t>(ws, L.o_nused);
+  pp.B = at<int32_t>(ws, L.o_Bp);
+  pp.flags = at<int32_t>(ws, L.o_flags);
+  pp.dirty = at<int32_t>(ws, L.o_dirty);
+  pp.ndirty = at<int32_t>(ws, L.o_ndirty);
+  return pp;
+}
+
+int rank_smem(int64_t n) {
+  int64_t N2 = 1;
+  while (N2 < n) N2 <<= 1;
+  return (int)(N2 * 12 + 4 * (kRankThreads + 1) + 64);
+}
+
+// B(m) = floor(m^alpha) for m = 0..n, written into the workspace.
+int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
+  std::vector<int32_t> Bt((size_t)L.n + 1);
+  for (int64_t m = 0; m <= L.n; ++m) Bt[(size_t)m] = m > 0 ? host_B(m, alpha) : 0;
+  // pageable source: the call returns after the data has been staged
+  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt.data(), sizeof(int32_t) * Bt.size(),
+                          cudaMemcpyHostToDevice, st));
+  return GMINE_OK;
+}
+
+// Ranks and equipartitions of the clean variables (slots 0..p-1).
+int prepare_variables(const double* d_vars, void* ws, const Layout& L, double alpha,
+                      cudaStream_t st) {
+  int rc = upload_Btab(ws, L, alpha, st);
+  if (rc != GMINE_OK) return rc;
+  const int n = (int)L.n;
+  k_tables<<<(n + 256) / 256, 256, 0, st>>>(n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32),
+                                             at<double>(ws, L.o_lnt));
+  GM_CUDA(cudaGetLastError());
+  if (L.p > 0) {
+    k_nonfinite<<<(unsigned)((L.p + 7) / 8), 256, 0, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf));
+    GM_CUDA(cudaGetLastError());
+    const int smem = rank_smem(L.n);
+    GM_CUDA(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PairPrep pp = pair_prep(ws, L);
+    k_rank<<<(unsigned)L.p, kRankThreads, smem, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf),
+                                                      nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0,
+                                                      rank_data(ws, L));
+    GM_CUDA(cudaGetLastError());
+    if (L.tb.R > 0) {
+      const int64_t work = L.p * L.tb.R;
+      k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
+          0, L.p, L.p, at<int32_t>(ws, L.o_Btab), nullptr, rank_data(ws, L), equi_data(ws, L));
+      GM_CUDA(cudaGetLastError());
+    }
+  }
+  return GMINE_OK;
+}
+
+bool plausible_device_ptr(const void* p) { return p != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int gmine_abi_version(void) { return GMINE_ABI_VERSION; }
+
+int gmine_check_param(const gmine_param* param) {
+  if (!param) return GMINE_E_ARG;
+  if (!(param->alpha > 0.0 && param->alpha <= 1.0)) return GMINE_E_PARAM;
+  if (!(param->c > 0.0) || !std::isfinite(param->c)) return GMINE_E_PARAM;
+  return GMINE_OK;
+}
+
+const char* gmine_strerror(int status) {
+  switch (status) {
+    case GMINE_OK: return "ok";
+    case GMINE_E_PARAM: return "invalid parameters: need 0 < alpha <= 1 and finite c > 0";
+    case GMINE_E_TOO_FEW: return "too few usable samples (need n >= 4 and B >= 4)";
+    case GMINE_E_CONSTANT: return "a variable is constant on the used samples";
+    case GMINE_E_NOMEM: return "allocation failed";
+    case GMINE_E_ARG: return "invalid argument";
+    case GMINE_E_WORKSPACE: return "workspace smaller than gmine_plan reported";
+    case GMINE_E_CUDA: return cudaGetErrorString(last_cuda_error());
+    case GMINE_E_LIMIT: return "size beyond the limits of this build";
+    case GMINE_E_NODEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int gmine_B(int64_t n, double alpha) { return n > 0 ? host_B(n, alpha) : 0; }
+
+int64_t gmine_m_cells(int32_t B) { return host_cells(B); }
+
+int gmine_plan(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
+               int32_t flags, int64_t* m_cells_per_pair, int64_t* workspace_bytes) {
+  Layout L;
+  const int rc = make_layout(p, n, n_pairs, param, precision, flags, &L);
+  if (rc != GMINE_OK) return rc;
+  if (m_cells_per_pair) *m_cells_per_pair = L.cells_max;
+  if (workspace_bytes) *workspace_bytes = L.total;
+  return GMINE_OK;
+}
+
+int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int32_t* d_pairs,
+                           int64_t n_pairs, const gmine_param* param, int32_t precision,
+                           void* d_workspace, int64_t workspace_bytes, gmine_pair_score* d_scores,
+                           double* d_M, const gmine_trace* trace, void* stream) {
+  if (n_pairs > 0 && (!plausible_device_ptr(d_vars) || !d_pairs || !d_scores)) return GMINE_E_ARG;
+  if (!d_workspace) return GMINE_E_ARG;
+  const int32_t flags = trace ? GMINE_PLAN_TRACE : 0;
+  Layout L;
+  int rc = make_layout(p, n, n_pairs, param, precision, flags, &L);
+  if (rc != GMINE_OK) return rc;
+  if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
+  if (n_pairs == 0) return GMINE_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = d_workspace;
+  rc = prepare_variables(d_vars, ws, L, param->alpha, st);
+  if (rc != GMINE_OK) return rc;
+
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  const int rsmem = rank_smem(L.n);
+  for (int64_t pair0 = 0; pair0 < n_pairs; pair0 += L.chunk) {
+    const int64_t C = std::min(L.chunk, n_pairs - pair0);
+    PairPrep pp = pair_prep(ws, L);
+    GM_CUDA(cudaMemsetAsync(pp.ndirty, 0, 4, st));
+    k_pair_prep<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
+        d_pairs, pair0, C, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), at<int32_t>(ws, L.o_Btab), pp);
+    GM_CUDA(cudaGetLastError());
+    // pairs with missing samples: compacted per-pair ranks and equipartitions
+    k_rank<<<(unsigned)(2 * C), kRankThreads, rsmem, st>>>(
+        d_vars, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp,
+        at<int32_t>(ws, L.o_Btab), L.p, rank_data(ws, L));
+    GM_CUDA(cudaGetLastError());
+    if (L.tb.R > 0) {
+      const int64_t work = 2 * C * L.tb.R;
+      k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
+          L.p, 2 * C, L.p, at<int32_t>(ws, L.o_Btab), pp.ndirty, rank_data(ws, L),
+          equi_data(ws, L));
+      GM_CUDA(cudaGetLastError());
+    }
+    // the tasks
+    TaskParams P{};
+    P.rk = rank_data(ws, L);
+    P.eq = equi_data(ws, L);
+    P.pp = pp;
+    P.L64 = at<double>(ws, L.o_L64);
+    P.L32 = at<float>(ws, L.o_L32);
+    P.lnt = at<double>(ws, L.o_lnt);
+    P.Mo = at<double>(ws, L.o_Mo);
+    P.cells_max = (int)L.cells_max;
+    P.n = (int)L.n;
+    P.c = param->c;
+    P.chunk_pairs = C;
+    P.ntasks = 2 * (int64_t)L.tb.R * C;
+    P.queue = at<unsigned long long>(ws, L.o_queue);
+    P.scratch = at<char>(ws, L.o_scratch);
+    P.scratch_per_cta = L.S.scratch_total;
+    P.w_in_smem = L.w_in_smem ? 1 : 0;
+    P.smem_W_bytes = L.S.w_bytes;
+    P.kmax = L.tb.kmax;
+    P.cum_max = L.tb.cum_max;
+    if (trace) P.trace = *trace;
+    P.trace_pair0 = pair0;
+    P.trace_npairs = n_pairs;
+    GM_CUDA(cudaMemsetAsync(P.queue, 0, 8, st));
+    if (P.ntasks > 0) GM_CUDA(task_launch(fp32, L.task_ctas, kTaskThreads, L.S.total, st, P, L.S));
+    FinalParams F{};
+    F.Mo = P.Mo;
+    F.cells_max = P.cells_max;
+    F.pp = pp;
+    F.chunk_pairs = C;
+    F.pair0 = pair0;
+    F.scores = d_scores;
+    F.M = d_M;
+    F.m_stride = L.cells_max;
+    F.eq_yhat = P.eq.yhat;
+    F.R = P.eq.R;
+    k_final<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(F);
+    GM_CUDA(cudaGetLastError());
+  }
+  return GMINE_OK;
+}
+
+int gmine_compute_batch(const double* d_vars, int64_t p, int64_t n, const int32_t* d_pairs,
+                        int64_t n_pairs, const gmine_param* param, int32_t precision,
+                        void* d_workspace, int64_t workspace_bytes, gmine_pair_score* d_scores,
+                        double* d_M, void* stream) {
+  return gmine_compute_batch_ex(d_vars, p, n, d_pairs, n_pairs, param, precision, d_workspace,
+                                workspace_bytes, d_scores, d_M, nullptr, stream);
+}
+
+int gmine_compute_batch_host(const double* h_vars, int64_t p, int64_t n, const int32_t* h_pairs,
+                             int64_t n_pairs, const gmine_param* param, int32_t precision,
+                             void* d_workspace, int64_t workspace_bytes,
+                             gmine_pair_score* h_scores, double* h_M, void* stream) {
+  if (n_pairs > 0 && (!h_vars || !h_pairs || !h_scores)) return GMINE_E_ARG;
+  if (!d_workspace) return GMINE_E_ARG;
+  Layout L;
+  int rc = make_layout(p, n, n_pairs, param, precision, GMINE_PLAN_HOST_STAGING, &L);
+  if (rc != GMINE_OK) return rc;
+  if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
+  if (n_pairs == 0) return GMINE_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* dv = at<double>(d_workspace, L.o_hvars);
+  int32_t* dp = at<int32_t>(d_workspace, L.o_hpairs);
+  gmine_pair_score* ds = at<gmine_pair_score>(d_workspace, L.o_hscores);
+  double* dM = h_M ? at<double>(d_workspace, L.o_hM) : nullptr;
+  GM_CUDA(cudaMemcpyAsync(dv, h_vars, 8 * p * n, cudaMemcpyHostToDevice, st));
+  GM_CUDA(cudaMemcpyAsync(dp, h_pairs, 8 * n_pairs, cudaMemcpyHostToDevice, st));
+  rc = gmine_compute_batch(dv, p, n, dp, n_pairs, param, precision, d_workspace, workspace_bytes,
+                           ds, dM, stream);
+  if (rc != GMINE_OK) return rc;
+  GM_CUDA(cudaMemcpyAsync(h_scores, ds, sizeof(gmine_pair_score) * n_pairs,
+                          cudaMemcpyDeviceToHost, st));
+  if (h_M) GM_CUDA(cudaMemcpyAsync(h_M, dM, 8 * n_pairs * L.cells_max, cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  return GMINE_OK;
+}
+
+int gmine_rank(const double* d_vars, int64_t p, int64_t n, int32_t* d_perm, int32_t* d_rank,
+               int32_t* d_groups, void* d_workspace, int64_t workspace_bytes, void* stream) {
+  if (!d_vars || !d_perm || !d_rank || !d_groups || !d_workspace) return GMINE_E_ARG;
+  gmine_param prm{0.6, 15.0};
+  Layout L;
+  int rc = make_layout(p, n, 0, &prm, GMINE_PLAIN_FP64, 0, &L);
+  if (rc != GMINE_OK) return rc;
+  if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
+  if (p == 0 || n == 0) return GMINE_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st);
+  if (rc != GMINE_OK) return rc;
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)p);
+  k_rank_export<<<grid, 256, 0, st>>>(rank_data(d_workspace, L), p, d_rank, d_perm, d_groups);
+  GM_CUDA(cudaGetLastError());
+  return GMINE_OK;
+}
+
+int gmine_equipartition(const double* d_vars, int64_t p, int64_t n, int32_t y, int32_t* d_Q,
+                        int32_t* d_yhat, void* d_workspace, int64_t workspace_bytes,
+                        void* stream) {
+  if (!d_vars || !d_Q || !d_yhat || !d_workspace || y < 1) return GMINE_E_ARG;
+  gmine_param prm{0.6, 15.0};
+  Layout L;
+  int rc = make_layout(p, n, 0, &prm, GMINE_PLAIN_FP64, 0, &L);
+  if (rc != GMINE_OK) return rc;
+  if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
+  if (p == 0 || n == 0) return GMINE_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st);
+  if (rc != GMINE_OK) return rc;
+  // one row count y for every variable: reuse the bounds rows of y = 2
+  // as output space through a dedicated single-y kernel
+  EquiData eq1;
+  eq1.bounds = at<int32_t>(d_workspace, L.o_bounds);
+  eq1.yhat = at<int32_t>(d_workspace, L.o_yhat);
+  eq1.R = 1;
+  eq1.bstride = y + 1;
+  if ((int64_t)p * (y + 1) > (int64_t)L.slots * std::max(L.tb.R, 1) * (L.tb.R + 2))
+    return GMINE_E_LIMIT;
+  k_equi_single<<<(unsigned)((p + 127) / 128), 128, 0, st>>>(p, y, rank_data(d_workspace, L), eq1);
+  GM_CUDA(cudaGetLastError());
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)p);
+  k_equi_export<<<grid, 256, 0, st>>>(rank_data(d_workspace, L), eq1, p, 2, d_Q, d_yhat);
+  GM_CUDA(cudaGetLastError());
+  return GMINE_OK;
+}
+
+int gmine_score_pair_host(const double* h_x, const double* h_y, int64_t n,
+                          const gmine_param* param, int32_t precision, gmine_pair_score* out,
+                          double* M_out) {
+  if (!h_x || !h_y || !out || n < 0) return GMINE_E_ARG;
+  int64_t cells = 0, wsb = 0;
+  int rc = gmine_plan(2, n, 1, param, precision, GMINE_PLAN_HOST_STAGING, &cells, &wsb);
+  if (rc != GMINE_OK) return rc;
+  std::vector<double> vars((size_t)(2 * n));
+  if (n > 0) {
+    std::memcpy(vars.data(), h_x, sizeof(double) * n);
+    std::memcpy(vars.data() + n, h_y, sizeof(double) * n);
+  }
+  const int32_t pairs[2] = {0, 1};
+  void* ws = nullptr;
+  if (cudaMalloc(&ws, (size_t)wsb) != cudaSuccess) return GMINE_E_NOMEM;
+  std::vector<double> M((size_t)std::max<int64_t>(cells, 1));
+  rc = gmine_compute_batch_host(vars.data(), 2, n, pairs, 1, param, precision, ws, wsb, out,
+                                M.data(), nullptr);
+  cudaFree(ws);
+  if (rc == GMINE_OK && M_out) std::memcpy(M_out, M.data(), sizeof(double) * out->m_cells);
+  return rc;
+}
+
+double gmine_mic(const gmine_pair_score* s) { return s ? s->mic : 0.0; }
+double gmine_mas(const gmine_pair_score* s) { return s ? s->mas : 0.0; }
+double gmine_mev(const gmine_pair_score* s) { return s ? s->mev : 0.0; }
+double gmine_mcn(const gmine_pair_score* s) { return s ? s->mcn : 0.0; }
+
+}  // extern "C"

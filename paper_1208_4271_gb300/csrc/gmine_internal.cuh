@@ -1,0 +1,201 @@
+// gmine_internal.cuh -- device-side building blocks shared by the libgmine
+// kernels (never by the CPU oracle).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gmine.h"
+
+namespace gm {
+
+constexpr int kWarp = 32;
+constexpr int kMaxRankN = 16384;  // largest slot sorted in shared memory
+
+// ---------------------------------------------------------------------------
+// Ordering key of a double: unsigned integers compare like the doubles, -0.0
+// and +0.0 get the same key (they are equal values, hence one tie group).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t order_key(double v) {
+  if (v == 0.0) v = 0.0;
+  uint64_t b = static_cast<uint64_t>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of `n` int flags/counts held in shared memory
+// (in place).  Each thread scans a contiguous chunk; chunk totals are scanned
+// by warp 0.  `tmp` needs blockDim.x + 1 ints.  Returns the total.  All
+// threads of the block must call it.
+// ---------------------------------------------------------------------------
+__device__ inline int block_exclusive_scan(int* a, int n, int* tmp) {
+  const int T = blockDim.x;
+  const int tid = threadIdx.x;
+  const int per = (n + T - 1) / T;
+  const int lo = min(n, tid * per);
+  const int hi = min(n, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  tmp[tid] = s;
+  __syncthreads();
+  if (tid < kWarp) {
+    // warp 0 scans the T chunk totals, 32 at a time
+    int carry = 0;
+    for (int base = 0; base < T; base += kWarp) {
+      int v = (base + tid < T) ? tmp[base + tid] : 0;
+      int incl = v;
+#pragma unroll
+      for (int d = 1; d < kWarp; d <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (tid >= d) incl += o;
+      }
+      if (base + tid < T) tmp[base + tid] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, kWarp - 1);
+    }
+    if (tid == 0) tmp[T] = carry;
+  }
+  __syncthreads();
+  int run = tmp[tid];
+  for (int i = lo; i < hi; ++i) {
+    int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  const int total = tmp[T];
+  __syncthreads();
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// EquipartitionYAxis over tie groups (SOM Alg. 3; Appendix items 3-4).
+//
+// The n points are in sorted order; tie group g covers sorted positions
+// [gs[g], gs[g+1]) (gs[0] = 0, gs[G] = n) and grp[m] is the group of
+// position m.  With the current row starting at position R0 (1-based index
+// i = R0 + 1) and being row number `row` (1-based) of Y, the desired size is
+// d = (n - R0) / (Y - row + 1); group S, starting at position P_S with |S|
+// points, opens a new row iff '#' = P_S - R0 != 0 and
+// |# + |S| - d| >= |# - d|, i.e. iff 2# + |S| >= 2d, i.e. iff
+//     (P_S + P_S+|S| - 2 R0) * (Y - row + 1) >= 2 (n - R0)
+// in exact integers.  The left side grows strictly with the group, so the
+// first such group is found directly: with Tp = 2 R0 + ceil(2 (n - R0) /
+// (Y - row + 1)) and p* = floor((Tp - 1) / 2), no group before grp[p*]
+// qualifies and every group after it does.  So the next row starts at
+// group grp[p*] if that group qualifies, else at grp[p*] + 1 (never before
+// the second group of the row).
+//
+// Writes the row starts bounds[0..yhat] (bounds[yhat] = n) and returns yhat.
+// Works on shared or global arrays (generic pointers).
+// ---------------------------------------------------------------------------
+__device__ inline int equipartition_bounds(const int* gs, const int* grp, int G,
+                                           int n, int Y, int* bounds) {
+  int R0 = 0, g0 = 0, row = 1;
+  bounds[0] = 0;
+  while (true) {
+    const long long mult = (long long)(Y - row + 1);
+    const long long thr = 2LL * (long long)(n - R0);
+    const long long Tp = 2LL * R0 + (thr + mult - 1) / mult;
+    long long ps = (Tp - 1) / 2;
+    if (ps > n - 1) ps = n - 1;
+    int gc = grp[ps];
+    if (gc < g0 + 1) gc = g0 + 1;
+    if (gc >= G) break;
+    if ((long long)gs[gc] + (long long)gs[gc + 1] < Tp) {
+      ++gc;
+      if (gc >= G) break;
+    }
+    R0 = gs[gc];
+    g0 = gc;
+    bounds[row] = R0;
+    ++row;
+  }
+  bounds[row] = n;
+  return row;
+}
+
+// khat = max(floor(c * floor(B / y)), 1) (Appendix item 7: khat = c x)
+__device__ __forceinline__ int khat_of(int B, int y, double c) {
+  const int x = B / y;
+  const int k = (int)floor(c * (double)x);
+  return k < 1 ? 1 : k;
+}
+
+// first cell of row count y in the y-major layout of M
+__device__ __forceinline__ int row_offset(int B, int y) {
+  int off = 0;
+  for (int yy = 2; yy < y; ++yy) off += B / yy - 1;
+  return off;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel parameter blocks
+// ---------------------------------------------------------------------------
+
+// Per-slot rank data.  A slot is a clean variable (slot = variable index) or
+// one side of a pair with missing samples (slot >= p, compacted samples).
+struct RankData {
+  int32_t* perm;     // [slots][n] sorted position -> sample
+  int32_t* pos;      // [slots][n] sample -> sorted position
+  int32_t* grp;      // [slots][n] sorted position -> tie group
+  int32_t* gstart;   // [slots][n+1] group starts
+  int32_t* ngroups;  // [slots]
+  int32_t* nslot;    // [slots] samples in the slot
+  int64_t stride;    // n
+};
+
+struct EquiData {
+  int32_t* bounds;   // [slots][R][bstride] row starts, sorted positions
+  int32_t* yhat;     // [slots][R]
+  int R;             // row counts y = 2 .. R + 1
+  int bstride;       // R + 2
+};
+
+struct PairPrep {
+  int32_t* slot;     // [chunk][2] slot of X and of Y
+  int32_t* n_used;   // [chunk]
+  int32_t* B;        // [chunk]
+  int32_t* flags;    // [chunk] status bits (1 << GMINE_E_*)
+  int32_t* dirty;    // [chunk] chunk-local indices of pairs with missing samples
+  int32_t* ndirty;   // [1]
+};
+
+struct TaskParams {
+  RankData rk;
+  EquiData eq;
+  PairPrep pp;
+  const double* L64;   // [n+1] m ln m
+  const float* L32;    // [n+1] (float) m ln m
+  const double* lnt;   // [n+1] ln m
+  double* Mo;          // [chunk][2][cells_max] normalised M_o per orientation
+  int cells_max;
+  int n;               // samples per variable (full)
+  double c;
+  int64_t chunk_pairs; // pairs in this chunk
+  int64_t ntasks;      // 2 * R * chunk_pairs
+  unsigned long long* queue;  // atomic task counter
+  char* scratch;       // per-CTA global scratch
+  int64_t scratch_per_cta;
+  int w_in_smem;       // 1: DP tables fit the shared-memory plan
+  int smem_W_bytes;    // bytes reserved for the DP tables in shared memory
+  int kmax;            // largest superclump count of any task
+  int cum_max;         // largest yhat * (k + 1) of any task
+  // trace (all NULL when off)
+  gmine_trace trace;
+  int64_t trace_pair0; // first pair of this chunk in the batch
+  int64_t trace_npairs;
+};
+
+struct FinalParams {
+  const double* Mo;
+  int cells_max;
+  PairPrep pp;
+  int64_t chunk_pairs;
+  int64_t pair0;
+  gmine_pair_score* scores;
+  double* M;           // may be NULL
+  int64_t m_stride;
+  const int32_t* eq_yhat;  // [slots][R] rows used per (slot, y)
+  int R;
+};
+
+}  // namespace gm

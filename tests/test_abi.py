@@ -1,0 +1,70 @@
+"""The C ABI library loads and exports every entry point that include/gmine.h
+declares; host-only calls behave as documented (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_4271_gb300 import build as libbuild
+from paper_1208_4271_gb300 import gmine
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gmine.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(gmine_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return gmine.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_abi_version_and_struct_sizes(lib):
+    assert lib.gmine_abi_version() == 1
+    assert gmine.SCORE_DTYPE.itemsize == 72
+    assert ctypes.sizeof(gmine.Trace) == 64
+
+
+def test_check_param_matches_documented_ranges(lib):
+    assert gmine.check_param(0.6, 15.0) == gmine.OK
+    assert gmine.check_param(1.0, 0.5) == gmine.OK
+    for a, c in [(0.0, 15), (-0.1, 15), (1.01, 15), (0.6, 0.0), (0.6, -1), (0.6, float("inf")),
+                 (float("nan"), 15), (0.6, float("nan"))]:
+        assert gmine.check_param(a, c) == gmine.E_PARAM
+    assert lib.gmine_check_param(None) == gmine.E_ARG
+
+
+def test_B_and_cells_agree_with_oracle(lib):
+    for n in (4, 10, 16, 300, 1000, 1001, 1340, 16384, 100000):
+        for a in (0.5, 0.55, 0.6, 0.75, 1.0):
+            assert gmine.B_of(n, a) == oracle.B_of(n, a)
+    for B in range(0, 200):
+        assert gmine.m_cells(B) == oracle.m_cells(B)
+
+
+def test_strerror_texts(lib):
+    for s in range(0, 10):
+        assert isinstance(gmine.strerror(s), str) and gmine.strerror(s)
+    assert "unknown" in gmine.strerror(12345)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(gmine, "_lib", None)
+    monkeypatch.setattr(gmine, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError):
+        gmine.lib()
