@@ -1,0 +1,354 @@
+"""Benchmark: MINE pairs/s at n = 1340, alpha = 0.6, c = 15 (all pairs of
+2000 synthetic microarray-shaped variables, 1,999,000 pairs per step).
+
+Our arm (default): the batched GB300 path through the libgmine C ABI, FP32
+DP with FP64 re-scoring of each chosen partition (`value`), with the plain
+FP64 DP measured beside it on a subset of the same pairs.  One step = one
+whole gmine_compute_batch over every pair of the batch (ranks, equipartition,
+clumps/superclumps, DP, M and the four statistics), inputs resident in HBM.
+
+Reference arm (--impl reference): the FP64 CPU oracle on this host's cores,
+each step a bounded sample of the same pairs.
+
+One JSON line is printed by rank 0.  Under torchrun every rank computes its
+own independently seeded copy of the workload (pairs are independent: weak
+scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MINE pairs/sec at n=1340 α=0.6 c=15: batched FP32-DP vs plain FP64, same GPU"
+ALPHA = 0.6
+C = 15.0
+N_SAMPLES = 1340
+N_VARS = 2000
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gmine", choices=["gmine", "reference"])
+    ap.add_argument("--vars", type=int, default=N_VARS,
+                    help="variables of the all-pairs workload (2000 = the metric's workload)")
+    ap.add_argument("--fp64-vars", type=int, default=200,
+                    help="variables whose all pairs time the plain FP64 path")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(rank, n_vars):
+    from paper_1208_4271_gb300 import workloads
+    V, P = workloads.config3(p=n_vars, n=N_SAMPLES, seed_salt=rank)
+    return V, P
+
+
+def oracle_sample(V, P, cpu_seconds, rng_seed=0):
+    """Time the FP64 CPU oracle on a bounded random sample of the pairs."""
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    probe = P[rng.choice(P.shape[0], min(P.shape[0], 2 * threads), replace=False)]
+    t0 = time.perf_counter()
+    oracle.score_batch(V, probe, ALPHA, C, nthreads=threads)
+    rate = probe.shape[0] / max(time.perf_counter() - t0, 1e-6)
+    m = int(min(P.shape[0], max(threads, rate * cpu_seconds)))
+    sample = P[rng.choice(P.shape[0], m, replace=False)]
+    t0 = time.perf_counter()
+    oracle.score_batch(V, sample, ALPHA, C, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "sample": "%d random pairs of the %d-variable all-pairs workload (n=%d), "
+                      "FP64 oracle, OpenMP over pairs, %.1f s" % (m, V.shape[0], V.shape[1], dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    V, P = workload(0, args.vars)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(V, P, args.cpu_seconds / max(args.steps, 1), rng_seed=i)
+        if i >= args.warmup:
+            steps.append(r)
+    value = statistics.mean(s["value"] for s in steps)
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(float(s["sample"].split()[0]) / s["value"] for s in steps) / len(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "all pairs of %d variables x n=%d (config 3), alpha=%g, c=%g"
+                                   % (args.vars, N_SAMPLES, ALPHA, C)},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": steps[0]["cores"],
+                             "kind": "oracle", "sample": steps[0]["sample"]},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1208_4271_gb300 import gmine
+
+    V, P = workload(rank, args.vars)
+    p, n = V.shape
+    npairs = P.shape[0]
+    Vd = torch.from_numpy(V).to(dev)
+    Pd = torch.from_numpy(P).to(dev)
+    prec = gmine.FP32_DP_FP64_RESCORE
+    ws = gmine.Workspace(p, n, npairs, ALPHA, C, prec, device=dev)
+    scores = torch.empty((npairs, gmine.SCORE_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    meas = gmine.Measure(device=dev)
+
+    def step(measure=True):
+        rc = gmine.lib().gmine_compute_batch_ex(
+            gmine._dptr(Vd), p, n, gmine._dptr(Pd), npairs,
+            gmine.ctypes.byref(gmine.Param(ALPHA, C)), prec, ws.ptr, ws.nbytes,
+            gmine._dptr(scores), None, gmine.ctypes.byref(meas.trace) if measure else None,
+            gmine._stream_ptr(stream))
+        gmine._check(rc, "gmine_compute_batch_ex")
+
+    for _ in range(args.warmup):
+        step(measure=False)
+        flush.zero_()
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dp_ms = 0.0
+    cand = 0
+    tasks = 0
+    launches = 0
+    dp_launches = 0
+    elapsed = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        step(measure=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        elapsed += e0.elapsed_time(e1)
+        dp_ms += meas.dp_ms
+        dp_launches += meas.dp_launches
+        launches += meas.kernel_launches
+        cand += int(meas.counters[0].item())
+        tasks += int(meas.counters[1].item())
+    barrier()
+    clk = clocks.stop()
+    ms_step = elapsed / args.steps
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step_max = float(t.item())
+    value = world * npairs / (ms_step_max / 1e3)
+
+    # the plain FP64 DP on all pairs of the first fp64_vars variables
+    fp64 = None
+    if args.fp64_vars > 1:
+        sub = min(args.fp64_vars, p)
+        Ps = torch.from_numpy(gmine_all_pairs(sub)).to(dev)
+        ws64 = gmine.Workspace(p, n, Ps.shape[0], ALPHA, C, gmine.PLAIN_FP64, device=dev)
+        sc64 = torch.empty((Ps.shape[0], gmine.SCORE_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+
+        def step64():
+            rc = gmine.lib().gmine_compute_batch(
+                gmine._dptr(Vd), p, n, gmine._dptr(Ps), Ps.shape[0],
+                gmine.ctypes.byref(gmine.Param(ALPHA, C)), gmine.PLAIN_FP64, ws64.ptr, ws64.nbytes,
+                gmine._dptr(sc64), None, gmine._stream_ptr(stream))
+            gmine._check(rc, "gmine_compute_batch")
+        step64()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        step64()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": Ps.shape[0] / (ms64 / 1e3), "unit": "pairs/s",
+                "sample": "all %d pairs of the first %d variables, one step after one warm-up"
+                          % (Ps.shape[0], sub)}
+        del ws64
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hv = torch.from_numpy(V).pin_memory()
+        hp = torch.from_numpy(P).pin_memory()
+        hs = torch.empty((npairs, gmine.SCORE_DTYPE.itemsize), dtype=torch.uint8).pin_memory()
+        wsh = gmine.Workspace(p, n, npairs, ALPHA, C, prec, gmine.PLAN_HOST_STAGING, device=dev)
+
+        def step_host():
+            rc = gmine.lib().gmine_compute_batch_host(
+                gmine.ctypes.c_void_p(hv.data_ptr()), p, n, gmine.ctypes.c_void_p(hp.data_ptr()),
+                npairs, gmine.ctypes.byref(gmine.Param(ALPHA, C)), prec, wsh.ptr, wsh.nbytes,
+                gmine.ctypes.c_void_p(hs.data_ptr()), None, gmine._stream_ptr(stream))
+            gmine._check(rc, "gmine_compute_batch_host")
+        step_host()
+        times = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            step_host()
+            times.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(times)
+        e2e = {"value": world * npairs / e2e_s, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(V.nbytes + P.nbytes),
+               "d2h_bytes_per_step": int(npairs * gmine.SCORE_DTYPE.itemsize)}
+        del wsh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(V, P, args.cpu_seconds)
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    # one subtract (FADD) and one max (FMNMX) per DP step on the 128 FP32
+    # lanes of each SM at the maximum SM clock
+    peak = sms * 128 * fmax * 1e6 / 2.0 / 1e12
+    dp_launch_ms = dp_ms / max(dp_launches, 1)
+    achieved = (cand / max(dp_launches, 1)) / (dp_launch_ms / 1e3) / 1e12 if dp_ms > 0 else 0.0
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "all pairs of %d variables x n=%d (config 3: log-normal "
+                                   "expression, 40 co-regulated modules), alpha=%g, c=%g"
+                                   % (p, n, ALPHA, C),
+                       "pairs_per_gpu": npairs, "dp": "fp32 with int32 counts, fp64 re-score",
+                       "l2": "256 MiB buffer written between timed steps"},
+            "plain_fp64": fp64,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcand/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "kernel": "k_dp<float,40>",
+                         "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr per DP step"
+                                       % (sms, fmax),
+                         "dp_candidates_per_step": cand // max(args.steps, 1),
+                         "dp_kernel_ms_per_step": dp_ms / args.steps,
+                         "dp_launches_per_step": dp_launches // args.steps,
+                         "tasks_per_step": tasks // args.steps},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def gmine_all_pairs(p):
+    from paper_1208_4271_gb300 import workloads
+    return workloads.all_pairs(p)
+
+
+if __name__ == "__main__":
+    main()

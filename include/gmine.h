@@ -112,6 +112,15 @@ typedef struct {
     double *d_I;          /* [tasks][I_stride] I(l) for l = 2..x            */
     int32_t I_stride;
     int32_t reserved;
+    int64_t *d_counters;  /* [2] device: subtract-and-max steps of the DP and
+                             tasks run; zeroed by the call                  */
+    double *h_dp_ms;      /* host: if not NULL the call times each launch of
+                             the DP kernel with CUDA events on `stream`,
+                             synchronises the stream before returning, and
+                             stores the summed milliseconds here           */
+    int32_t *h_dp_launches;  /* host: number of DP kernel launches timed   */
+    int32_t *h_kernel_launches;  /* host: if not NULL, every kernel launch of
+                                    the call is counted here               */
 } gmine_trace;
 
 /* ---- parameters, errors ------------------------------------------------ */
@@ -137,7 +146,8 @@ int64_t gmine_m_cells(int32_t B);
 #define GMINE_PLAN_HOST_STAGING 1   /* workspace also holds device copies of
                                        the inputs and outputs, as needed by
                                        gmine_compute_batch_host */
-#define GMINE_PLAN_TRACE 2          /* room for gmine_trace scratch tables */
+#define GMINE_PLAN_TRACE 2          /* accepted for compatibility; the trace
+                                       needs no extra workspace */
 
 /* Sizes for a batch of n_pairs pairs over p variables of n samples.
    *m_cells_per_pair: cells of M reserved per pair (pair i's cells start at

@@ -65,108 +65,200 @@ int device_info(DeviceInfo* d) {
   return GMINE_OK;
 }
 
-// Shape bounds of the tasks of a batch with n samples and parameters (B, c).
+// Shape bounds of the tasks with row counts y in [ylo, yhi] of a batch with
+// n samples and parameters (B, c).
 struct TaskBounds {
-  int B, R, xmax, kmax, cum_max;
-  int64_t welems;
+  int B, R, xmax, kmax, cum_max, lmax;
 };
 
-TaskBounds task_bounds(int n, int B, double c) {
+TaskBounds task_bounds(int n, int B, double c, int ylo, int yhi) {
   TaskBounds tb{};
   tb.B = B;
   tb.R = std::max(B / 2 - 1, 0);
-  tb.xmax = B / 2;
-  for (int y = 2; y <= B / 2; ++y) {
+  for (int y = std::max(ylo, 2); y <= std::min(yhi, B / 2); ++y) {
     const int kk = std::min(host_khat(B, y, c), n);
     const int x = B / y;
+    tb.xmax = std::max(tb.xmax, x);
     tb.kmax = std::max(tb.kmax, kk);
     tb.cum_max = std::max(tb.cum_max, y * (kk + 1));
-    tb.welems = std::max(tb.welems, (int64_t)(std::min(x, kk) + 1) * (kk + 1));
+    tb.lmax = std::max(tb.lmax, std::min(x, kk));
   }
   return tb;
 }
 
-SmemPlan make_plan(int n, const TaskBounds& tb, bool fp32, bool trace, int smem_optin,
-                   bool* w_in_smem) {
-  SmemPlan S{};
+// Shared-memory plan of the DP kernel for the tasks bounded by tb.
+// *r_in_smem / *l_in_smem tell where the R table and the entropy table live.
+DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int smem_optin,
+                    bool* r_in_smem) {
   const int rs = fp32 ? 4 : 8;
-  int o = 0;
-  S.offP_Qs = o; o = align16i(o + 2LL * n);
-  S.offP_q = o; o = align16i(o + 2LL * n);
-  S.offP_mixed = o; o = align16i(o + (int64_t)n);
-  S.offP_cflag = o; o = align16i(o + (int64_t)n);
-  S.offP_grpU = o; o = align16i(o + 4LL * n);
-  S.offP_cgrp = o; o = align16i(o + 4LL * n);
-  S.offP_cstart = o; o = align16i(o + 4LL * (n + 1));
-  S.sizeP = o;
-  int k = 0;
-  const int keb = k; k = align16i(k + 4LL * (tb.B / 2 + 2));
-  const int kscb = k; k = align16i(k + 4LL * (tb.kmax + 1));
-  const int kcum = k; k = align16i(k + 4LL * std::max(tb.cum_max, 1));
-  const int kE = k; k = align16i(k + (int64_t)rs * (tb.kmax + 1));
-  const int kV = k; k = align16i(k + (int64_t)rs * (tb.xmax + 1));
-  const int kVa = k; k = align16i(k + 4LL * (tb.xmax + 1));
-  const int ktmp = k; k = align16i(k + 4LL * (kTaskThreads + 1));
-  const int sizeK = k;
-  // DP tables: W (real) and, for the float path, the int16 argmax table
-  int64_t wbytes = ((tb.welems * rs + 15) & ~15LL);
-  if (fp32) wbytes += ((tb.welems * 2 + 15) & ~15LL);
-  const int reserve = 1024;  // static shared memory of the kernel
-  // prefer both regions in shared memory, then the DP tables alone, then
-  // the prologue alone, then neither (per-CTA global scratch instead)
-  bool p_smem, w_smem;
-  if (std::max<int64_t>(S.sizeP, wbytes) + sizeK + reserve <= smem_optin) {
-    p_smem = true; w_smem = true;
-  } else if (wbytes + sizeK + reserve <= smem_optin) {
-    p_smem = false; w_smem = true;
-  } else if ((int64_t)S.sizeP + sizeK + reserve <= smem_optin) {
-    p_smem = true; w_smem = false;
+  const int NW = threads / 32;
+  DPPlan S{};
+  S.LS = std::max(4, (tb.lmax - 1 + 3) & ~3);
+  S.LX = std::max(4, (tb.lmax + 3) & ~3);
+  S.xmax = std::max(tb.xmax, 2);
+  const int64_t rbytes = (int64_t)(tb.kmax + 1) * S.LS * rs;
+  const int64_t lbytes = (int64_t)(n + 1) * rs;
+  // traceback scratch aliased on the X buffers once the DP is done
+  const int64_t cuts_b = (4LL * NW * S.xmax + 15) & ~int64_t(15);
+  const int64_t I_b = (8LL * (S.xmax + 1) + 15) & ~int64_t(15);
+  const int64_t ecol_b = 8LL * NW * (S.xmax + 1);
+  S.off_I_rel = (int)cuts_b;
+  S.off_ecol_rel = (int)(cuts_b + I_b);
+  const int64_t xbytes = std::max<int64_t>((int64_t)2 * 32 * S.LX * rs, cuts_b + I_b + ecol_b);
+  int64_t fixed = 0;
+  auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
+  S.off_X = add(xbytes);
+  S.off_Eb = add((int64_t)32 * 33 * rs);
+  S.off_Rtop = add((int64_t)(tb.kmax + 1) * rs);
+  S.off_scb = add(4LL * (tb.kmax + 1));
+  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
+  const int reserve = 1024;
+  const bool in_smem = fixed + rbytes + lbytes + 32 + reserve <= smem_optin;
+  *r_in_smem = in_smem;
+  int64_t o = fixed;
+  if (in_smem) {
+    S.off_L = (int)o;
+    o = (o + lbytes + 15) & ~int64_t(15);
+    S.off_R = (int)o;
+    o = (o + rbytes + 15) & ~int64_t(15);
   } else {
-    p_smem = false; w_smem = false;
+    S.off_L = -1;
+    S.off_R = -1;
   }
-  *w_in_smem = w_smem;
-  S.p_in_smem = p_smem ? 1 : 0;
-  S.w_bytes = w_smem ? (int)wbytes : 0;
-  const int offK = align16i(std::max<int64_t>(p_smem ? S.sizeP : 0, S.w_bytes));
-  S.offK_eb = offK + keb;
-  S.offK_scb = offK + kscb;
-  S.offK_cum = offK + kcum;
-  S.offK_Ecol = offK + kE;
-  S.offK_V = offK + kV;
-  S.offK_Varg = offK + kVa;
-  S.offK_tmp = offK + ktmp;
-  S.total = offK + sizeK;
-  S.scratch_P = p_smem ? 0 : align256(S.sizeP);
-  S.scratch_tables = w_smem ? 0 : (int64_t)align256(wbytes);
-  S.scratch_A32 = (!fp32 && trace) ? align256(tb.welems * 4) : 0;
-  S.scratch_cuts = align256((int64_t)tb.xmax * std::max(tb.xmax - 1, 1) / 2 * 4 + 4);
-  S.scratch_total = S.scratch_P + S.scratch_tables + S.scratch_A32 + S.scratch_cuts;
+  S.total = (int)o;
   return S;
 }
+
+// Shared-memory layout of the partition kernel for n samples: the CTA's
+// pi / tie-group maps, then one region per warp.
+struct PartPlan {
+  int warps, warp_smem, off_pi, off_gU, off_warps, total;
+  int off_Qs, off_q, off_cgrp, off_cstart, off_scb, off_mixed, off_eb;
+};
+
+PartPlan make_part_plan(int n, const TaskBounds& tb, int warps) {
+  PartPlan pp{};
+  pp.warps = warps;
+  int o = 0;
+  auto add = [&](int64_t b) { const int at = o; o = (int)((o + b + 15) & ~int64_t(15)); return at; };
+  pp.off_pi = add(2LL * n);
+  pp.off_gU = add(2LL * n);
+  pp.off_warps = o;
+  o = 0;
+  pp.off_Qs = add(std::max<int64_t>(2LL * n, 4LL * std::max(tb.cum_max, 1)));  // Qs, then counts
+  pp.off_q = add(2LL * n);
+  pp.off_cgrp = add(2LL * n);
+  pp.off_cstart = add(2LL * (n + 1));
+  pp.off_scb = add(2LL * (tb.kmax + 1));
+  pp.off_mixed = add(4LL * ((n + 31) / 32 + 1));
+  pp.off_eb = add(4LL * (tb.B / 2 + 2));
+  pp.warp_smem = o;
+  pp.total = pp.off_warps + warps * pp.warp_smem;
+  return pp;
+}
+
+// Shared-memory layout of the warp-per-task DP kernel.
+SmallPlan make_small_plan(int n, const TaskBounds& tb, bool fp32, int warps) {
+  const int rs = fp32 ? 4 : 8;
+  SmallPlan S{};
+  S.LW = tb.xmax + 1;
+  int o = 0;
+  auto add = [&](int64_t b) { const int at = o; o = (int)((o + b + 15) & ~int64_t(15)); return at; };
+  S.off_L = add((int64_t)(n + 1) * rs);
+  S.off_warps = o;
+  o = 0;
+  S.off_W = add((int64_t)(tb.kmax + 1) * S.LW * rs);
+  S.off_A = add((int64_t)(tb.kmax + 1) * S.LW * 2);
+  S.off_Ecol = add((int64_t)(tb.kmax + 1) * rs);
+  S.off_scb = add(4LL * (tb.kmax + 1));
+  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
+  S.off_V = add((int64_t)S.LW * rs);
+  S.off_Va = add(4LL * S.LW);
+  S.off_I = add(8LL * S.LW);
+  S.off_cuts = add(4LL * S.LW * S.LW);
+  S.warp_smem = o;
+  S.total = S.off_warps + warps * S.warp_smem;
+  return S;
+}
+
+constexpr int kDPThreadsBig = 256;
+constexpr int kDPThreadsSmall = 128;
+constexpr int64_t kRecBudget = 3LL << 30;  // record bytes per chunk
+constexpr int kMaxDPGroups = 16;
+
+// One launch of the DP kernel: the tasks with row counts y in [ylo, yhi],
+// whose column counts share one level group (levels kept in registers).
+struct DPGroup {
+  int ylo, yhi, lev, threads, ctas;
+  bool rsm;
+  bool small;      // warp-per-task kernel
+  DPPlan S;
+  SmallPlan SS;
+  int64_t scratch_per_cta, o_scratch;
+};
 
 // Workspace layout of a batch (byte offsets from the workspace base).
 struct Layout {
   int64_t n, p, n_pairs, chunk, slots;
   int B;
-  TaskBounds tb;
-  SmemPlan S;
-  bool w_in_smem;
-  int task_ctas;
+  TaskBounds tb;        // all row counts
+  int ngroups;
+  DPGroup grp[kMaxDPGroups];
+  PartPlan part;
+  int part_ctas;
+  int64_t rec_per_orient;
   int64_t cells_max;
   int64_t o_Btab, o_L64, o_L32, o_lnt, o_nf;
   int64_t o_perm, o_pos, o_grp, o_gstart, o_ngroups, o_nslot;
   int64_t o_bounds, o_yhat;
   int64_t o_slot, o_nused, o_Bp, o_flags, o_dirty, o_ndirty;
-  int64_t o_Mo, o_queue, o_scratch;
+  int64_t o_rec, o_Mo, o_queue;
   int64_t o_hvars, o_hpairs, o_hscores, o_hM;
   int64_t total;
 };
 
-int task_occupancy(bool fp32, int smem, int* blocks) {
-  const cudaError_t e = task_configure(fp32, smem, kTaskThreads, blocks);
+int dp_occupancy(bool fp32, bool rsm, int lev, int smem, int threads, int* blocks) {
+  const cudaError_t e = dp_configure(fp32, rsm, lev, smem, threads, blocks);
   if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
   return GMINE_OK;
 }
+
+int64_t dp_scratch(const TaskBounds& tb, const DPPlan& S, bool fp32, bool r_smem) {
+  const int rs = fp32 ? 4 : 8;
+  // one spare row: a level group may read past the last row's columns
+  return r_smem ? 0 : align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+}
+
+// CUDA events around the DP launches of one call (h_dp_ms of gmine_trace).
+struct DPTiming {
+  std::vector<cudaEvent_t> ev;
+  ~DPTiming() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  cudaError_t pair(cudaEvent_t* a, cudaEvent_t* b) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      const cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+    }
+    *a = ev[ev.size() - 2];
+    *b = ev[ev.size() - 1];
+    return cudaSuccess;
+  }
+  int launches() const { return (int)(ev.size() / 2); }
+  cudaError_t total_ms(double* out) const {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0.f;
+      const cudaError_t r = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      if (r != cudaSuccess) return r;
+      t += ms;
+    }
+    *out = t;
+    return cudaSuccess;
+  }
+};
 
 int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
                 int32_t flags, Layout* L) {
@@ -182,20 +274,87 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   L->n = n;
   L->p = p;
   L->n_pairs = n_pairs;
-  L->chunk = std::max<int64_t>(1, std::min<int64_t>(n_pairs, kChunkPairs));
-  L->slots = p + 2 * L->chunk;
   L->B = n > 0 ? host_B(n, param->alpha) : 0;
-  L->tb = task_bounds((int)n, L->B, param->c);
+  const int B = L->B;
+  L->tb = task_bounds((int)n, B, param->c, 2, B / 2);
   const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
-  const bool trace = (flags & GMINE_PLAN_TRACE) != 0;
-  L->S = make_plan((int)n, L->tb, fp32, trace, dev.smem_optin, &L->w_in_smem);
-  if (L->S.total > dev.smem_optin) return GMINE_E_LIMIT;
-  int blocks = 0;
-  rc = task_occupancy(fp32, L->S.total, &blocks);
-  if (rc != GMINE_OK) return rc;
-  if (blocks < 1) return GMINE_E_LIMIT;
-  L->task_ctas = blocks * dev.sms;
-  L->cells_max = std::max<int64_t>(host_cells(L->B), 1);
+  // DP launch groups: consecutive row counts whose x - 1 share a level group
+  L->ngroups = 0;
+  for (int y = 2; y <= B / 2; ++y) {
+    const int lev = dp_level_group(fp32, std::max(B / y - 1, 1));
+    if (L->ngroups > 0 && L->grp[L->ngroups - 1].lev == lev) {
+      L->grp[L->ngroups - 1].yhi = y;
+    } else {
+      if (L->ngroups == kMaxDPGroups) return GMINE_E_LIMIT;
+      DPGroup& g = L->grp[L->ngroups++];
+      g = DPGroup{};
+      g.ylo = g.yhi = y;
+      g.lev = lev;
+    }
+  }
+  for (int gi = 0; gi < L->ngroups; ++gi) {
+    DPGroup& g = L->grp[gi];
+    const TaskBounds tg = task_bounds((int)n, B, param->c, g.ylo, g.yhi);
+    if (g.lev <= 8 && tg.kmax <= 256 && tg.xmax <= 9) {
+      // few columns: one warp per task, as many warps per CTA as fit
+      for (int w = 4; w >= 1 && !g.small; w >>= 1) {
+        const SmallPlan sp = make_small_plan((int)n, tg, fp32, w);
+        if (sp.total + 1024 <= dev.smem_optin) {
+          g.small = true;
+          g.threads = 32 * w;
+          g.SS = sp;
+        }
+      }
+      if (g.small) {
+        g.scratch_per_cta = 0;
+        continue;
+      }
+    }
+    g.threads = tg.kmax >= 128 ? kDPThreadsBig : kDPThreadsSmall;
+    g.S = make_dp_plan((int)n, tg, fp32, g.threads, dev.smem_optin, &g.rsm);
+    if (g.S.total > dev.smem_optin) return GMINE_E_LIMIT;
+    int blocks = 0;
+    rc = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
+    if (rc != GMINE_OK) return rc;
+    if (blocks < 1) return GMINE_E_LIMIT;
+    g.ctas = blocks * dev.sms;
+    g.scratch_per_cta = dp_scratch(tg, g.S, fp32, g.rsm);
+  }
+  {
+    // the warp-per-task kernel is shared by its groups: one attribute (the
+    // largest plan), then each group's occupancy at its own size
+    int smax = 0;
+    for (int gi = 0; gi < L->ngroups; ++gi)
+      if (L->grp[gi].small) smax = std::max(smax, L->grp[gi].SS.total);
+    for (int gi = 0; gi < L->ngroups; ++gi) {
+      DPGroup& g = L->grp[gi];
+      if (!g.small) continue;
+      int blocks = 0;
+      cudaError_t e = dp_small_configure(fp32, smax, g.threads, &blocks);
+      if (e == cudaSuccess) e = dp_small_occupancy(fp32, g.SS.total, g.threads, &blocks);
+      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+      if (blocks < 1) return GMINE_E_LIMIT;
+      g.ctas = blocks * dev.sms;
+    }
+  }
+  L->part = make_part_plan((int)n, L->tb, 4);
+  if (L->part.total + 1024 > dev.smem_optin) L->part = make_part_plan((int)n, L->tb, 1);
+  if (L->part.total + 1024 > dev.smem_optin) return GMINE_E_LIMIT;
+  {
+    int pb = 0;
+    const int smem = L->part.total;
+    cudaError_t e = cudaFuncSetAttribute(k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_partition, 32 * L->part.warps, smem);
+    if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+    if (pb < 1) return GMINE_E_LIMIT;
+    L->part_ctas = pb * dev.sms;
+  }
+  L->rec_per_orient = std::max<int64_t>(rec_offset(B, (int)n, param->c, B / 2 + 1), 4);
+  const int64_t rec_pair = 2 * L->rec_per_orient * 4;
+  L->chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n_pairs, 32768),
+                                                    kRecBudget / rec_pair));
+  L->slots = p + 2 * L->chunk;
+  L->cells_max = std::max<int64_t>(host_cells(B), 1);
 
   const int64_t S = L->slots;
   const int R = std::max(L->tb.R, 1);
@@ -225,9 +384,11 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   L->o_flags = take(4 * L->chunk);
   L->o_dirty = take(4 * L->chunk);
   L->o_ndirty = take(4);
+  L->o_rec = take(L->chunk * rec_pair);
   L->o_Mo = take(8 * L->chunk * 2 * L->cells_max);
-  L->o_queue = take(8);
-  L->o_scratch = take(L->S.scratch_total * L->task_ctas);
+  L->o_queue = take(8 * (kMaxDPGroups + 1));
+  for (int gi = 0; gi < L->ngroups; ++gi)
+    L->grp[gi].o_scratch = take(L->grp[gi].scratch_per_cta * L->grp[gi].ctas);
   if (flags & GMINE_PLAN_HOST_STAGING) {
     L->o_hvars = take(8 * p * n);
     L->o_hpairs = take(4 * 2 * n_pairs);
@@ -295,16 +456,18 @@ int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
 
 // Ranks and equipartitions of the clean variables (slots 0..p-1).
 int prepare_variables(const double* d_vars, void* ws, const Layout& L, double alpha,
-                      cudaStream_t st) {
+                      cudaStream_t st, int* launches) {
   int rc = upload_Btab(ws, L, alpha, st);
   if (rc != GMINE_OK) return rc;
   const int n = (int)L.n;
   k_tables<<<(n + 256) / 256, 256, 0, st>>>(n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32),
                                              at<double>(ws, L.o_lnt));
   GM_CUDA(cudaGetLastError());
+  ++*launches;
   if (L.p > 0) {
     k_nonfinite<<<(unsigned)((L.p + 7) / 8), 256, 0, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf));
     GM_CUDA(cudaGetLastError());
+    ++*launches;
     const int smem = rank_smem(L.n);
     GM_CUDA(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PairPrep pp = pair_prep(ws, L);
@@ -312,11 +475,13 @@ int prepare_variables(const double* d_vars, void* ws, const Layout& L, double al
                                                       nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0,
                                                       rank_data(ws, L));
     GM_CUDA(cudaGetLastError());
+    ++*launches;
     if (L.tb.R > 0) {
       const int64_t work = L.p * L.tb.R;
       k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
           0, L.p, L.p, at<int32_t>(ws, L.o_Btab), nullptr, rank_data(ws, L), equi_data(ws, L));
       GM_CUDA(cudaGetLastError());
+      ++*launches;
     }
   }
   return GMINE_OK;
@@ -381,11 +546,15 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   if (n_pairs == 0) return GMINE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* ws = d_workspace;
-  rc = prepare_variables(d_vars, ws, L, param->alpha, st);
+  int launches = 0;
+  rc = prepare_variables(d_vars, ws, L, param->alpha, st, &launches);
   if (rc != GMINE_OK) return rc;
 
   const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
   const int rsmem = rank_smem(L.n);
+  if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
+  DPTiming tim;
+  DPTiming* timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
   for (int64_t pair0 = 0; pair0 < n_pairs; pair0 += L.chunk) {
     const int64_t C = std::min(L.chunk, n_pairs - pair0);
     PairPrep pp = pair_prep(ws, L);
@@ -393,57 +562,114 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
     k_pair_prep<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
         d_pairs, pair0, C, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), at<int32_t>(ws, L.o_Btab), pp);
     GM_CUDA(cudaGetLastError());
+    ++launches;
     // pairs with missing samples: compacted per-pair ranks and equipartitions
     k_rank<<<(unsigned)(2 * C), kRankThreads, rsmem, st>>>(
         d_vars, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp,
         at<int32_t>(ws, L.o_Btab), L.p, rank_data(ws, L));
     GM_CUDA(cudaGetLastError());
+    ++launches;
     if (L.tb.R > 0) {
       const int64_t work = 2 * C * L.tb.R;
       k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
           L.p, 2 * C, L.p, at<int32_t>(ws, L.o_Btab), pp.ndirty, rank_data(ws, L),
           equi_data(ws, L));
       GM_CUDA(cudaGetLastError());
+      ++launches;
     }
-    // the tasks
-    TaskParams P{};
-    P.rk = rank_data(ws, L);
-    P.eq = equi_data(ws, L);
-    P.pp = pp;
-    P.L64 = at<double>(ws, L.o_L64);
-    P.L32 = at<float>(ws, L.o_L32);
-    P.lnt = at<double>(ws, L.o_lnt);
-    P.Mo = at<double>(ws, L.o_Mo);
-    P.cells_max = (int)L.cells_max;
-    P.n = (int)L.n;
-    P.c = param->c;
-    P.chunk_pairs = C;
-    P.ntasks = 2 * (int64_t)L.tb.R * C;
-    P.queue = at<unsigned long long>(ws, L.o_queue);
-    P.scratch = at<char>(ws, L.o_scratch);
-    P.scratch_per_cta = L.S.scratch_total;
-    P.w_in_smem = L.w_in_smem ? 1 : 0;
-    P.smem_W_bytes = L.S.w_bytes;
-    P.kmax = L.tb.kmax;
-    P.cum_max = L.tb.cum_max;
-    if (trace) P.trace = *trace;
-    P.trace_pair0 = pair0;
-    P.trace_npairs = n_pairs;
-    GM_CUDA(cudaMemsetAsync(P.queue, 0, 8, st));
-    if (P.ntasks > 0) GM_CUDA(task_launch(fp32, L.task_ctas, kTaskThreads, L.S.total, st, P, L.S));
+    // partition of every task of the chunk
+    const int64_t ntasks = 2 * (int64_t)L.tb.R * C;
+    if (ntasks > 0) {
+      PartParams Q{};
+      Q.rk = rank_data(ws, L);
+      Q.eq = equi_data(ws, L);
+      Q.pp = pp;
+      Q.L64 = at<double>(ws, L.o_L64);
+      Q.lnt = at<double>(ws, L.o_lnt);
+      Q.rec = at<int32_t>(ws, L.o_rec);
+      Q.rec_per_orient = L.rec_per_orient;
+      Q.B_full = L.B;
+      Q.n_full = (int)L.n;
+      Q.c = param->c;
+      Q.chunk_pairs = C;
+      Q.queue = at<unsigned long long>(ws, L.o_queue) + kMaxDPGroups;
+      Q.off_pi = L.part.off_pi;
+      Q.off_gU = L.part.off_gU;
+      Q.off_warps = L.part.off_warps;
+      Q.warp_smem = L.part.warp_smem;
+      Q.off_Qs = L.part.off_Qs;
+      Q.off_q = L.part.off_q;
+      Q.off_cgrp = L.part.off_cgrp;
+      Q.off_cstart = L.part.off_cstart;
+      Q.off_scb = L.part.off_scb;
+      Q.off_mixed = L.part.off_mixed;
+      Q.off_eb = L.part.off_eb;
+      GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
+      k_partition<<<L.part_ctas, 32 * L.part.warps, L.part.total, st>>>(Q);
+      GM_CUDA(cudaGetLastError());
+      ++launches;
+      // the dynamic program: large row counts... small row counts
+      DPParams P{};
+      P.pp = pp;
+      P.rec = Q.rec;
+      P.rec_per_orient = L.rec_per_orient;
+      P.B_full = L.B;
+      P.n_full = (int)L.n;
+      P.c = param->c;
+      P.L64 = at<double>(ws, L.o_L64);
+      P.L32 = at<float>(ws, L.o_L32);
+      P.lnt = at<double>(ws, L.o_lnt);
+      P.Mo = at<double>(ws, L.o_Mo);
+      P.cells_max = (int)L.cells_max;
+      P.chunk_pairs = C;
+      P.counters = trace ? trace->d_counters : nullptr;
+      if (trace) P.trace = *trace;
+      P.trace_pair0 = pair0;
+      P.trace_npairs = n_pairs;
+      unsigned long long* qs = at<unsigned long long>(ws, L.o_queue);
+      GM_CUDA(cudaMemsetAsync(qs, 0, 8 * kMaxDPGroups, st));
+      for (int gi = 0; gi < L.ngroups; ++gi) {
+        const DPGroup& g = L.grp[gi];
+        P.task_begin = 2 * (int64_t)(g.ylo - 2) * C;
+        P.task_end = 2 * (int64_t)(g.yhi - 1) * C;
+        P.queue = qs + gi;
+        P.scratch = at<char>(ws, g.o_scratch);
+        P.scratch_per_cta = g.scratch_per_cta;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timing) {
+          GM_CUDA(timing->pair(&e0, &e1));
+          GM_CUDA(cudaEventRecord(e0, st));
+        }
+        if (g.small)
+          GM_CUDA(dp_small_launch(fp32, g.ctas, g.threads, g.SS.total, st, P, g.SS));
+        else
+          GM_CUDA(dp_launch(fp32, g.rsm, g.lev, g.ctas, g.threads, g.S.total, st, P, g.S));
+        ++launches;
+        if (timing) GM_CUDA(cudaEventRecord(e1, st));
+      }
+    }
     FinalParams F{};
-    F.Mo = P.Mo;
-    F.cells_max = P.cells_max;
+    F.Mo = at<double>(ws, L.o_Mo);
+    F.cells_max = (int)L.cells_max;
     F.pp = pp;
     F.chunk_pairs = C;
     F.pair0 = pair0;
     F.scores = d_scores;
     F.M = d_M;
     F.m_stride = L.cells_max;
-    F.eq_yhat = P.eq.yhat;
-    F.R = P.eq.R;
+    F.eq_yhat = equi_data(ws, L).yhat;
+    F.R = equi_data(ws, L).R;
     k_final<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(F);
     GM_CUDA(cudaGetLastError());
+    ++launches;
+  }
+  if (trace && trace->h_kernel_launches) *trace->h_kernel_launches = launches;
+  if (timing) {
+    GM_CUDA(cudaStreamSynchronize(st));
+    double ms = 0.0;
+    GM_CUDA(timing->total_ms(&ms));
+    *trace->h_dp_ms = ms;
+    if (trace->h_dp_launches) *trace->h_dp_launches = timing->launches();
   }
   return GMINE_OK;
 }
@@ -494,7 +720,8 @@ int gmine_rank(const double* d_vars, int64_t p, int64_t n, int32_t* d_perm, int3
   if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
   if (p == 0 || n == 0) return GMINE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st);
+  int launches = 0;
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st, &launches);
   if (rc != GMINE_OK) return rc;
   dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)p);
   k_rank_export<<<grid, 256, 0, st>>>(rank_data(d_workspace, L), p, d_rank, d_perm, d_groups);
@@ -513,7 +740,8 @@ int gmine_equipartition(const double* d_vars, int64_t p, int64_t n, int32_t y, i
   if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
   if (p == 0 || n == 0) return GMINE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st);
+  int launches = 0;
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st, &launches);
   if (rc != GMINE_OK) return rc;
   // one row count y for every variable: reuse the bounds rows of y = 2
   // as output space through a dedicated single-y kernel

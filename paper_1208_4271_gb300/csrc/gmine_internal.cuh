@@ -87,8 +87,9 @@ __device__ inline int block_exclusive_scan(int* a, int n, int* tmp) {
 // Writes the row starts bounds[0..yhat] (bounds[yhat] = n) and returns yhat.
 // Works on shared or global arrays (generic pointers).
 // ---------------------------------------------------------------------------
-__device__ inline int equipartition_bounds(const int* gs, const int* grp, int G,
-                                           int n, int Y, int* bounds) {
+template <typename GS, typename GRP, typename OUT>
+__device__ inline int equipartition_bounds_t(const GS* gs, const GRP* grp, int G, int n, int Y,
+                                             OUT* bounds) {
   int R0 = 0, g0 = 0, row = 1;
   bounds[0] = 0;
   while (true) {
@@ -97,27 +98,54 @@ __device__ inline int equipartition_bounds(const int* gs, const int* grp, int G,
     const long long Tp = 2LL * R0 + (thr + mult - 1) / mult;
     long long ps = (Tp - 1) / 2;
     if (ps > n - 1) ps = n - 1;
-    int gc = grp[ps];
+    int gc = (int)grp[ps];
     if (gc < g0 + 1) gc = g0 + 1;
     if (gc >= G) break;
     if ((long long)gs[gc] + (long long)gs[gc + 1] < Tp) {
       ++gc;
       if (gc >= G) break;
     }
-    R0 = gs[gc];
+    R0 = (int)gs[gc];
     g0 = gc;
-    bounds[row] = R0;
+    bounds[row] = (OUT)R0;
     ++row;
   }
-  bounds[row] = n;
+  bounds[row] = (OUT)n;
   return row;
 }
 
+__device__ inline int equipartition_bounds(const int* gs, const int* grp, int G, int n, int Y,
+                                           int* bounds) {
+  return equipartition_bounds_t<int, int, int>(gs, grp, G, n, Y, bounds);
+}
+
+__device__ inline int equipartition_bounds_u16(const uint16_t* gs, const uint16_t* grp, int G,
+                                               int n, int Y, uint16_t* bounds) {
+  return equipartition_bounds_t<uint16_t, uint16_t, uint16_t>(gs, grp, G, n, Y, bounds);
+}
+
 // khat = max(floor(c * floor(B / y)), 1) (Appendix item 7: khat = c x)
-__device__ __forceinline__ int khat_of(int B, int y, double c) {
+__host__ __device__ __forceinline__ int khat_of(int B, int y, double c) {
   const int x = B / y;
   const int k = (int)floor(c * (double)x);
   return k < 1 ? 1 : k;
+}
+
+// Record of one task written by the partition kernel (int32 units, a
+// multiple of 4): header (k, yhat, clumps, 0, H(Q) as double), superclump
+// ends c_0..c_k, counts cum[r][t] for r < yhat.  Sized for the largest k and
+// yhat a task with row count y can have in a batch of n samples, B = B(n).
+__host__ __device__ __forceinline__ int64_t rec_size(int B, int n, double c, int y) {
+  int kk = khat_of(B, y, c);
+  if (kk > n) kk = n;
+  const int64_t sz = 6 + (int64_t)(kk + 1) * (y + 1);
+  return (sz + 3) & ~int64_t(3);
+}
+
+__host__ __device__ __forceinline__ int64_t rec_offset(int B, int n, double c, int y) {
+  int64_t off = 0;
+  for (int yy = 2; yy < y; ++yy) off += rec_size(B, n, c, yy);
+  return off;
 }
 
 // first cell of row count y in the y-major layout of M
@@ -159,30 +187,62 @@ struct PairPrep {
   int32_t* ndirty;   // [1]
 };
 
-struct TaskParams {
+struct PartParams {
   RankData rk;
   EquiData eq;
   PairPrep pp;
   const double* L64;   // [n+1] m ln m
-  const float* L32;    // [n+1] (float) m ln m
   const double* lnt;   // [n+1] ln m
+  int32_t* rec;        // task records, [chunk][2][rec_per_orient] ints
+  int64_t rec_per_orient;
+  int B_full, n_full;  // B and n of the full sample count
+  double c;
+  int64_t chunk_pairs;
+  unsigned long long* queue;  // atomic (pair, orientation) counter
+  int off_pi, off_gU;  // shared by the CTA: [n] uint16 each
+  int off_warps;       // first per-warp region
+  int warp_smem;       // bytes of shared memory per warp
+  int off_Qs, off_q, off_cgrp, off_cstart, off_scb, off_mixed, off_eb;  // within a warp region
+};
+
+struct DPParams {
+  PairPrep pp;
+  const int32_t* rec;
+  int64_t rec_per_orient;
+  int B_full, n_full;
+  double c;
+  const double* L64;
+  const float* L32;
+  const double* lnt;
   double* Mo;          // [chunk][2][cells_max] normalised M_o per orientation
   int cells_max;
-  int n;               // samples per variable (full)
-  double c;
-  int64_t chunk_pairs; // pairs in this chunk
-  int64_t ntasks;      // 2 * R * chunk_pairs
-  unsigned long long* queue;  // atomic task counter
-  char* scratch;       // per-CTA global scratch
+  int64_t chunk_pairs;
+  int64_t task_begin, task_end;  // tasks of this launch
+  unsigned long long* queue;
+  int64_t* counters;             // [2] DP candidates, tasks (may be NULL)
+  char* scratch;                 // per-CTA R tables that do not fit in smem
   int64_t scratch_per_cta;
-  int w_in_smem;       // 1: DP tables fit the shared-memory plan
-  int smem_W_bytes;    // bytes reserved for the DP tables in shared memory
-  int kmax;            // largest superclump count of any task
-  int cum_max;         // largest yhat * (k + 1) of any task
-  // trace (all NULL when off)
   gmine_trace trace;
-  int64_t trace_pair0; // first pair of this chunk in the batch
-  int64_t trace_npairs;
+  int64_t trace_pair0, trace_npairs;
+};
+
+// Shared-memory layout of the warp-per-task DP kernel (byte offsets): the
+// CTA's entropy table, then one region per warp.
+struct SmallPlan {
+  int off_L, off_warps, warp_smem;
+  int off_W, off_A, off_Ecol, off_scb, off_cum, off_V, off_Va, off_I, off_cuts;
+  int LW;     // row stride of the W / A tables (levels 0..xmax)
+  int total;
+};
+
+// Shared-memory layout of the DP kernel (byte offsets).
+struct DPPlan {
+  int off_R, off_Rtop, off_X, off_Eb, off_L, off_scb, off_cum;
+  int off_I_rel, off_ecol_rel;  // traceback scratch inside the X region
+  int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4
+  int LX;     // row stride of the X buffers: levels 1..lmax, multiple of 4
+  int xmax;   // largest x of the launch
+  int total;
 };
 
 struct FinalParams {

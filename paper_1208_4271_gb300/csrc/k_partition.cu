@@ -1,0 +1,194 @@
+// k_partition.cu -- the partitions of every task (pair, orientation o, row
+// count y): the row variable's EquipartitionYAxis map in the column
+// variable's order, GetClumpsPartition, GetSuperclumpsPartition with
+// khat = c * floor(B/y), the per-superclump prefix counts cum[r][t] and H(Q)
+// (Appendix items 5-7 and 10a, the two algorithm listings).
+//
+// One CTA per (pair, o): the map pi[m] = position in the row variable's
+// order of the m-th point in the column variable's order, and the column
+// variable's tie groups, are gathered once into shared memory and serve all
+// row counts; each warp then takes row counts y one after another.  The
+// result of every task is a record in global memory that the DP kernels
+// read:
+//   int32 [0] k, [1] yhat, [2] clumps, [3] unused, [4..5] H(Q) as double,
+//   [6 .. 6+k] superclump ends c_0..c_k (sorted positions),
+//   then cum[r][t] for r < yhat, t = 0..k (row-major, stride k+1).
+#include "gmine_internal.cuh"
+#include "kernels.h"
+
+namespace gm {
+
+__device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
+  return (bm[g >> 5] >> (g & 31)) & 1u;
+}
+
+__global__ void __launch_bounds__(128) k_partition(PartParams P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ long long s_job;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int NWp = blockDim.x >> 5;
+  uint16_t* pi = reinterpret_cast<uint16_t*>(sm + P.off_pi);   // [n] U position -> V position
+  uint16_t* gU = reinterpret_cast<uint16_t*>(sm + P.off_gU);   // [n] U position -> tie group
+  unsigned char* my = sm + P.off_warps + (int64_t)wib * P.warp_smem;
+  uint16_t* Qs = reinterpret_cast<uint16_t*>(my + P.off_Qs);     // V position -> row
+  int* cnt = reinterpret_cast<int*>(my + P.off_Qs);              // (aliases Qs)
+  uint16_t* q = reinterpret_cast<uint16_t*>(my + P.off_q);       // U position -> row
+  uint16_t* cgrp = reinterpret_cast<uint16_t*>(my + P.off_cgrp); // U position -> clump
+  uint16_t* cstart = reinterpret_cast<uint16_t*>(my + P.off_cstart);
+  uint16_t* scb = reinterpret_cast<uint16_t*>(my + P.off_scb);
+  uint32_t* mixed = reinterpret_cast<uint32_t*>(my + P.off_mixed);
+  int* eb = reinterpret_cast<int*>(my + P.off_eb);
+
+  const int64_t C = P.chunk_pairs;
+  const int R = P.eq.R;
+  const int64_t st = P.rk.stride;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = (long long)atomicAdd(P.queue, 1ull);
+    __syncthreads();
+    const int64_t job = s_job;
+    __syncthreads();
+    if (job >= 2 * C) break;
+    const int64_t pl = job >> 1;
+    const int o = (int)(job & 1);
+    const int n = P.pp.n_used[pl];
+    const int B = P.pp.B[pl];
+    int32_t* rec0 = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient;
+    if (n < 4 || B < 4) {
+      for (int y = 2 + (int)threadIdx.x; y <= P.B_full / 2; y += blockDim.x) {
+        int32_t* rec = rec0 + rec_offset(P.B_full, P.n_full, P.c, y);
+        rec[0] = 0;
+        rec[1] = 0;
+        rec[2] = 0;
+      }
+      continue;
+    }
+    const int sU = P.pp.slot[2 * pl + o];
+    const int sV = P.pp.slot[2 * pl + (1 - o)];
+    const int32_t* permU = P.rk.perm + (int64_t)sU * st;
+    const int32_t* posV = P.rk.pos + (int64_t)sV * st;
+    const int32_t* grpU = P.rk.grp + (int64_t)sU * st;
+    const int GU = P.rk.ngroups[sU];
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      pi[m] = (uint16_t)posV[permU[m]];
+      gU[m] = (uint16_t)grpU[m];
+    }
+    __syncthreads();
+
+    for (int y = 2 + wib; y <= P.B_full / 2; y += NWp) {
+      int32_t* rec = rec0 + rec_offset(P.B_full, P.n_full, P.c, y);
+      if (y > B / 2) {  // fewer samples than the batch's n: no such task
+        if (lane == 0) {
+          rec[0] = 0;
+          rec[1] = 0;
+          rec[2] = 0;
+        }
+        continue;
+      }
+      const int yhat = P.eq.yhat[(int64_t)sV * R + (y - 2)];
+      const int32_t* gb = P.eq.bounds + ((int64_t)sV * R + (y - 2)) * P.eq.bstride;
+      for (int j = lane; j <= yhat; j += 32) eb[j] = gb[j];
+      for (int w = lane; w < (GU + 31) / 32; w += 32) mixed[w] = 0u;
+      __syncwarp();
+      // rows of the V-sorted positions, then of the U-sorted positions
+      for (int j = 0; j < yhat; ++j)
+        for (int p = eb[j] + lane; p < eb[j + 1]; p += 32) Qs[p] = (uint16_t)j;
+      __syncwarp();
+      for (int m = lane; m < n; m += 32) q[m] = Qs[pi[m]];
+      __syncwarp();
+      // x-tie runs whose rows are mixed get one fresh label (Algorithm
+      // GetClumpsPartition, first pass; one label per run)
+      for (int m = 1 + lane; m < n; m += 32) {
+        const int g = gU[m];
+        if (g == gU[m - 1] && q[m] != q[m - 1]) atomicOr(&mixed[g >> 5], 1u << (g & 31));
+      }
+      __syncwarp();
+      // a clump starts where the label changes (second pass): ballot per 32
+      int nc = 0;
+      for (int base = 0; base < n; base += 32) {
+        const int m = base + lane;
+        bool f = false;
+        if (m < n) {
+          if (m == 0) {
+            f = true;
+          } else {
+            const int g = gU[m], gp = gU[m - 1];
+            f = g != gp && (bit_of(mixed, g) || bit_of(mixed, gp) || q[m] != q[m - 1]);
+          }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, f);
+        const int before = __popc(mask & ((1u << lane) - 1u));
+        if (m < n) {
+          cgrp[m] = (uint16_t)(nc + before + (f ? 1 : 0) - 1);
+          if (f) cstart[nc + before] = (uint16_t)m;
+        }
+        nc += __popc(mask);
+      }
+      if (lane == 0) cstart[nc] = (uint16_t)n;
+      __syncwarp();
+      // superclumps: EquipartitionYAxis over the clumps (Algorithm
+      // GetSuperclumpsPartition), one row after another in lane 0
+      const int khat = khat_of(B, y, P.c);
+      int k;
+      const bool superclump = nc > khat;
+      if (superclump) {
+        int kk = 0;
+        if (lane == 0) kk = equipartition_bounds_u16(cstart, cgrp, nc, n, khat, scb);
+        k = __shfl_sync(0xffffffffu, kk, 0);
+      } else {
+        for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
+        k = nc;
+      }
+      const int ks = k + 1;
+      __syncwarp();
+      for (int i = lane; i < yhat * ks; i += 32) cnt[i] = 0;  // Qs is dead now
+      __syncwarp();
+      for (int m = lane; m < n; m += 32) {
+        int t;
+        if (superclump) {
+          int lo = 0, hi = k;  // largest t with scb[t] <= m
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if ((int)scb[mid] <= m) lo = mid; else hi = mid;
+          }
+          t = lo;
+        } else {
+          t = cgrp[m];
+        }
+        atomicAdd(&cnt[(int)q[m] * ks + t + 1], 1);
+      }
+      __syncwarp();
+      // prefix over superclumps, written to the record; row totals give H(Q)
+      int32_t* rcum = rec + 6 + ks;
+      double sL = 0.0;
+      for (int r = 0; r < yhat; ++r) {
+        int carry = 0;
+        for (int base = 0; base < ks; base += 32) {
+          const int i = base + lane;
+          const int v = i < ks ? cnt[r * ks + i] : 0;
+          int incl = v;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int oo = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += oo;
+          }
+          if (i < ks) rcum[r * ks + i] = carry + incl;
+          carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        sL += P.L64[carry];  // increasing r, as H(Q) is defined
+      }
+      for (int j = lane; j <= k; j += 32) rec[6 + j] = scb[j];
+      if (lane == 0) {
+        rec[0] = k;
+        rec[1] = yhat;
+        rec[2] = nc;
+        rec[3] = 0;
+        *reinterpret_cast<double*>(rec + 4) = P.lnt[n] - sL / (double)n;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gm

@@ -40,7 +40,9 @@ class Trace(ctypes.Structure):
                 ("d_clumps", ctypes.c_void_p), ("d_sc_ends", ctypes.c_void_p),
                 ("sc_stride", ctypes.c_int32), ("cut_stride", ctypes.c_int32),
                 ("d_cuts", ctypes.c_void_p), ("d_I", ctypes.c_void_p),
-                ("I_stride", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("I_stride", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("d_counters", ctypes.c_void_p), ("h_dp_ms", ctypes.c_void_p),
+                ("h_dp_launches", ctypes.c_void_p), ("h_kernel_launches", ctypes.c_void_p)]
 
 
 _lib = None
@@ -164,11 +166,41 @@ def alloc_trace(n_pairs, n, alpha, c, device="cuda"):
          "sc_ends": torch.full((tasks, st["sc_stride"]), -7, dtype=torch.int32, device=device),
          "cuts": torch.full((tasks, st["cut_stride"]), -7, dtype=torch.int32, device=device),
          "I": torch.full((tasks, st["I_stride"]), float("nan"), dtype=torch.float64, device=device)}
+    t["counters"] = torch.zeros(2, dtype=torch.int64, device=device)
     tr = Trace(_dptr(t["k"]), _dptr(t["yhat"]), _dptr(t["clumps"]), _dptr(t["sc_ends"]),
                st["sc_stride"], st["cut_stride"], _dptr(t["cuts"]), _dptr(t["I"]),
-               st["I_stride"], 0)
+               st["I_stride"], 0, _dptr(t["counters"]), None, None, None)
     t.update(st)
     return tr, t
+
+
+class Measure:
+    """Counters and DP kernel timing of one batch call (gmine_trace without
+    the per-task tables): subtract-and-max steps, tasks, summed DP kernel
+    milliseconds measured with CUDA events on the call's stream."""
+
+    def __init__(self, device="cuda"):
+        import torch
+        self.counters = torch.zeros(2, dtype=torch.int64, device=device)
+        self._ms = ctypes.c_double(0.0)
+        self._launches = ctypes.c_int32(0)
+        self._kernels = ctypes.c_int32(0)
+        self.trace = Trace(None, None, None, None, 0, 0, None, None, 0, 0,
+                           _dptr(self.counters), ctypes.cast(ctypes.byref(self._ms), ctypes.c_void_p),
+                           ctypes.cast(ctypes.byref(self._launches), ctypes.c_void_p),
+                           ctypes.cast(ctypes.byref(self._kernels), ctypes.c_void_p))
+
+    @property
+    def dp_ms(self):
+        return self._ms.value
+
+    @property
+    def dp_launches(self):
+        return self._launches.value
+
+    @property
+    def kernel_launches(self):
+        return self._kernels.value
 
 
 def compute_batch(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, want_M=True,

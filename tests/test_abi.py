@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_abi_version_and_struct_sizes(lib):
     assert lib.gmine_abi_version() == 1
     assert gmine.SCORE_DTYPE.itemsize == 72
-    assert ctypes.sizeof(gmine.Trace) == 64
+    assert ctypes.sizeof(gmine.Trace) == 96
 
 
 def test_check_param_matches_documented_ranges(lib):
