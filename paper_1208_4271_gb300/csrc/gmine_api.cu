@@ -446,10 +446,11 @@ int rank_smem(int64_t n) {
 
 // B(m) = floor(m^alpha) for m = 0..n, written into the workspace.
 int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
-  std::vector<int32_t> Bt((size_t)L.n + 1);
-  for (int64_t m = 0; m <= L.n; ++m) Bt[(size_t)m] = m > 0 ? host_B(m, alpha) : 0;
+  // n <= kMaxRankN: the table fits a stack buffer (no heap allocation)
+  int32_t Bt[kMaxRankN + 1];
+  for (int64_t m = 0; m <= L.n; ++m) Bt[m] = m > 0 ? host_B(m, alpha) : 0;
   // pageable source: the call returns after the data has been staged
-  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt.data(), sizeof(int32_t) * Bt.size(),
+  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt, sizeof(int32_t) * (size_t)(L.n + 1),
                           cudaMemcpyHostToDevice, st));
   return GMINE_OK;
 }
