@@ -186,6 +186,35 @@ int gmine_compute_batch_host(const double *h_vars, int64_t p, int64_t n,
                              gmine_pair_score *h_scores, double *h_M,
                              void *stream);
 
+/* ---- batch without a caller workspace ---------------------------------- */
+
+/* gmine_compute_batch with the working memory taken from a fixed array
+   inside the library (64 MiB per GPU) instead of a workspace from the
+   caller.  The paper has no counterpart of this call.
+   It serves callers that cannot allocate device memory: code hosted by an
+   application that owns the GPU's memory through its own pool and does not
+   let plug-ins call cudaMalloc, and code on a latency-critical path that
+   cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
+   The call allocates nothing.  Inputs and outputs are the caller's, exactly
+   as for gmine_compute_batch (d_M may be NULL).
+   - Limit: batches whose gmine_plan workspace exceeds 64 MiB are refused
+     with GMINE_E_WORKSPACE before anything is enqueued (a few hundred pairs
+     at n ~ 1000, or one pair up to a few thousand samples at alpha = 0.6).
+   - The first call on each device looks up the array's device address
+     (cudaGetSymbolAddress with that device current) and keeps it; make that
+     first call before any stream capture.
+   - Every call on a device shares the one array.  Its contents from an
+     earlier call do not matter (the computation initialises all it reads),
+     but calls whose work can overlap on the GPU (other streams, other host
+     threads) race on it: order them, e.g. on one stream.
+   The array stays allocated on every GPU where the call was used until the
+   process exits. */
+int gmine_compute_batch_static(const double *d_vars, int64_t p, int64_t n,
+                               const int32_t *d_pairs, int64_t n_pairs,
+                               const gmine_param *param, int32_t precision,
+                               gmine_pair_score *d_scores, double *d_M,
+                               void *stream);
+
 /* ---- single steps, the same kernels as the batch uses ------------------ */
 
 /* Tie-aware sort of every variable (finite samples; no NaN allowed):

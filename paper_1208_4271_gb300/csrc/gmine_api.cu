@@ -492,6 +492,10 @@ bool plausible_device_ptr(const void* p) { return p != nullptr; }
 
 }  // namespace
 
+namespace gm {
+void note_cuda_error(cudaError_t e) { last_cuda_error() = e; }
+}  // namespace gm
+
 extern "C" {
 
 int gmine_abi_version(void) { return GMINE_ABI_VERSION; }

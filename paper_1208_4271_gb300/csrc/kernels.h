@@ -37,4 +37,7 @@ cudaError_t dp_configure(bool fp32, bool rsm, int lev, int smem, int threads, in
 cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int smem,
                       cudaStream_t st, const DPParams& P, const DPPlan& S);
 
+// Records a CUDA error for gmine_strerror (host code outside gmine_api.cu).
+void note_cuda_error(cudaError_t e);
+
 }  // namespace gm

@@ -74,6 +74,8 @@ def lib():
                                              _i32, _vp, _i64, _vp, _vp, ctypes.POINTER(Trace), _vp]
         L.gmine_compute_batch_host.argtypes = [_vp, _i64, _i64, _vp, _i64, ctypes.POINTER(Param),
                                                _i32, _vp, _i64, _vp, _vp, _vp]
+        L.gmine_compute_batch_static.argtypes = [_vp, _i64, _i64, _vp, _i64, ctypes.POINTER(Param),
+                                                 _i32, _vp, _vp, _vp]
         L.gmine_rank.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp]
         L.gmine_equipartition.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64, _vp]
         L.gmine_score_pair_host.argtypes = [_vp, _vp, _i64, ctypes.POINTER(Param), _i32, _vp, _vp]
@@ -232,6 +234,27 @@ def compute_batch(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, want_M=
                                           ctypes.byref(trace), _stream_ptr(stream))
     _check(rc, "gmine_compute_batch")
     return scores[:n_pairs], M
+
+
+def compute_batch_static(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, want_M=True,
+                         stream=None):
+    """gmine_compute_batch_static: the batch with the library's own fixed
+    scratch array (no workspace allocated anywhere).  Returns (status, scores,
+    M); status GMINE_E_WORKSPACE means the batch needs more than the array."""
+    import torch
+    assert vars_.is_cuda and vars_.dtype == torch.float64 and vars_.is_contiguous()
+    assert pairs.is_cuda and pairs.dtype == torch.int32 and pairs.is_contiguous()
+    p, n = vars_.shape
+    n_pairs = pairs.shape[0]
+    cells = m_cells(B_of(max(n, 1), alpha)) if n > 0 else 1
+    scores = torch.zeros((max(n_pairs, 1), SCORE_DTYPE.itemsize), dtype=torch.uint8,
+                         device=vars_.device)
+    M = torch.zeros(max(n_pairs * max(cells, 1), 1), dtype=torch.float64,
+                    device=vars_.device) if want_M else None
+    rc = lib().gmine_compute_batch_static(_dptr(vars_), p, n, _dptr(pairs), n_pairs,
+                                          ctypes.byref(Param(alpha, c)), int(precision),
+                                          _dptr(scores), _dptr(M), _stream_ptr(stream))
+    return rc, scores[:n_pairs], M
 
 
 def scores_to_numpy(scores):
