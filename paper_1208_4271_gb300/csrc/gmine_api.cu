@@ -145,7 +145,7 @@ PartPlan make_part_plan(int n, const TaskBounds& tb, int warps) {
   pp.off_gU = add(2LL * n);
   pp.off_warps = o;
   o = 0;
-  pp.off_Qs = add(std::max<int64_t>(2LL * n, 4LL * std::max(tb.cum_max, 1)));  // Qs, then counts
+  pp.off_Qs = add(std::max<int64_t>(2LL * n, 2LL * std::max(tb.cum_max, 1) + 4));  // Qs, then counts
   pp.off_q = add(2LL * n);
   pp.off_cgrp = add(2LL * n);
   pp.off_cstart = add(2LL * (n + 1));
@@ -169,7 +169,8 @@ SmallPlan make_small_plan(int n, const TaskBounds& tb, bool fp32, int warps) {
   o = 0;
   S.off_W = add((int64_t)(tb.kmax + 1) * S.LW * rs);
   S.off_A = add((int64_t)(tb.kmax + 1) * S.LW * 2);
-  S.off_Ecol = add((int64_t)(tb.kmax + 1) * rs);
+  S.LE = (tb.kmax + 1 + 3) & ~3;
+  S.off_Ecol = add((int64_t)2 * S.LE * rs);
   S.off_scb = add(4LL * (tb.kmax + 1));
   S.off_cum = add(4LL * std::max(tb.cum_max, 1));
   S.off_V = add((int64_t)S.LW * rs);
@@ -178,6 +179,27 @@ SmallPlan make_small_plan(int n, const TaskBounds& tb, bool fp32, int warps) {
   S.off_cuts = add(4LL * S.LW * S.LW);
   S.warp_smem = o;
   S.total = S.off_warps + warps * S.warp_smem;
+  return S;
+}
+
+// Shared-memory layout of the level-major DP kernel for the tasks bounded by tb.
+MidPlan make_mid_plan(int n, const TaskBounds& tb, bool fp32, int threads) {
+  const int rs = fp32 ? 4 : 8;
+  const int NW = threads / 32;
+  MidPlan S{};
+  S.KS = (tb.kmax + 1 + 3) & ~3;
+  S.xmax = std::max(tb.xmax, 2);
+  int64_t o = 0;
+  auto add = [&](int64_t b) { const int64_t at = o; o = (o + b + 15) & ~int64_t(15); return (int)at; };
+  S.off_E = add((int64_t)tb.kmax * (tb.kmax + 1) / 2 * rs);
+  S.off_R = add((int64_t)(tb.lmax + 1) * S.KS * rs);
+  S.off_L = add((int64_t)(n + 1) * rs);
+  S.off_scb = add(4LL * (tb.kmax + 1));
+  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
+  S.off_I = add(8LL * (S.xmax + 1));
+  S.off_cuts = add(4LL * NW * S.xmax);
+  S.off_ecol = add(8LL * NW * (S.xmax + 1));
+  S.total = (int)std::min<int64_t>(o, 1LL << 30);
   return S;
 }
 
@@ -192,8 +214,10 @@ struct DPGroup {
   int ylo, yhi, lev, threads, ctas;
   bool rsm;
   bool small;      // warp-per-task kernel
+  bool mid;        // level-major kernel
   DPPlan S;
   SmallPlan SS;
+  MidPlan MS;
   int64_t scratch_per_cta, o_scratch;
 };
 
@@ -295,7 +319,20 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   for (int gi = 0; gi < L->ngroups; ++gi) {
     DPGroup& g = L->grp[gi];
     const TaskBounds tg = task_bounds((int)n, B, param->c, g.ylo, g.yhi);
-    if (g.lev <= 8 && tg.kmax <= 256 && tg.xmax <= 9) {
+    if (g.lev >= 8 && g.lev <= 12) {
+      // few levels, entropy triangle small enough for two CTAs per SM:
+      // level-major kernel (no chain along t)
+      const int th = tg.kmax >= 96 ? 256 : 128;
+      const MidPlan mp = make_mid_plan((int)n, tg, fp32, th);
+      if (2 * (mp.total + 1024) <= dev.smem_optin + 1024) {
+        g.mid = true;
+        g.threads = th;
+        g.MS = mp;
+        g.scratch_per_cta = 0;
+        continue;
+      }
+    }
+    if (g.lev <= 4 && tg.kmax <= 256 && tg.xmax <= 9) {
       // few columns: one warp per task, as many warps per CTA as fit
       for (int w = 4; w >= 1 && !g.small; w >>= 1) {
         const SmallPlan sp = make_small_plan((int)n, tg, fp32, w);
@@ -310,22 +347,52 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
         continue;
       }
     }
-    g.threads = tg.kmax >= 128 ? kDPThreadsBig : kDPThreadsSmall;
-    g.S = make_dp_plan((int)n, tg, fp32, g.threads, dev.smem_optin, &g.rsm);
-    if (g.S.total > dev.smem_optin) return GMINE_E_LIMIT;
-    int blocks = 0;
-    rc = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
-    if (rc != GMINE_OK) return rc;
-    if (blocks < 1) return GMINE_E_LIMIT;
-    g.ctas = blocks * dev.sms;
+    // CTA size: the one that keeps more warps resident per SM (more CTAs,
+    // i.e. more tasks in flight, on a tie: their sequential parts overlap)
+    {
+      int best_warps = -1;
+      for (int th : {kDPThreadsSmall, kDPThreadsBig}) {
+        bool rsm = false;
+        const DPPlan S = make_dp_plan((int)n, tg, fp32, th, dev.smem_optin, &rsm);
+        if (S.total > dev.smem_optin) continue;
+        int blocks = 0;
+        rc = dp_occupancy(fp32, rsm, g.lev, std::max(S.total, 1), th, &blocks);
+        if (rc != GMINE_OK) return rc;
+        if (blocks * th / 32 > best_warps) {
+          best_warps = blocks * th / 32;
+          g.threads = th;
+          g.S = S;
+          g.rsm = rsm;
+          g.ctas = blocks * dev.sms;
+        }
+      }
+      if (best_warps <= 0) return GMINE_E_LIMIT;
+      // the launch attribute must allow the chosen plan (the loop left the
+      // last candidate's size in place)
+      int blocks = 0;
+      rc = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
+      if (rc != GMINE_OK) return rc;
+    }
     g.scratch_per_cta = dp_scratch(tg, g.S, fp32, g.rsm);
   }
   {
     // the warp-per-task kernel is shared by its groups: one attribute (the
     // largest plan), then each group's occupancy at its own size
-    int smax = 0;
-    for (int gi = 0; gi < L->ngroups; ++gi)
+    int smax = 0, mmax = 0;
+    for (int gi = 0; gi < L->ngroups; ++gi) {
       if (L->grp[gi].small) smax = std::max(smax, L->grp[gi].SS.total);
+      if (L->grp[gi].mid) mmax = std::max(mmax, L->grp[gi].MS.total);
+    }
+    for (int gi = 0; gi < L->ngroups; ++gi) {
+      DPGroup& g = L->grp[gi];
+      if (!g.mid) continue;
+      int blocks = 0;
+      cudaError_t e = dp_mid_configure(fp32, mmax, g.threads, &blocks, true);
+      if (e == cudaSuccess) e = dp_mid_configure(fp32, g.MS.total, g.threads, &blocks, false);
+      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+      if (blocks < 1) return GMINE_E_LIMIT;
+      g.ctas = blocks * dev.sms;
+    }
     for (int gi = 0; gi < L->ngroups; ++gi) {
       DPGroup& g = L->grp[gi];
       if (!g.small) continue;
@@ -645,7 +712,9 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
           GM_CUDA(timing->pair(&e0, &e1));
           GM_CUDA(cudaEventRecord(e0, st));
         }
-        if (g.small)
+        if (g.mid)
+          GM_CUDA(dp_mid_launch(fp32, g.ctas, g.threads, g.MS.total, st, P, g.MS));
+        else if (g.small)
           GM_CUDA(dp_small_launch(fp32, g.ctas, g.threads, g.SS.total, st, P, g.SS));
         else
           GM_CUDA(dp_launch(fp32, g.rsm, g.lev, g.ctas, g.threads, g.S.total, st, P, g.S));

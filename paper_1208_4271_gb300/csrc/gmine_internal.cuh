@@ -90,18 +90,19 @@ __device__ inline int block_exclusive_scan(int* a, int n, int* tmp) {
 template <typename GS, typename GRP, typename OUT>
 __device__ inline int equipartition_bounds_t(const GS* gs, const GRP* grp, int G, int n, int Y,
                                              OUT* bounds) {
+  // n <= 2^29, so every quantity below fits 32-bit integers
   int R0 = 0, g0 = 0, row = 1;
   bounds[0] = 0;
   while (true) {
-    const long long mult = (long long)(Y - row + 1);
-    const long long thr = 2LL * (long long)(n - R0);
-    const long long Tp = 2LL * R0 + (thr + mult - 1) / mult;
-    long long ps = (Tp - 1) / 2;
+    const int mult = Y - row + 1;
+    const int thr = 2 * (n - R0);
+    const int Tp = 2 * R0 + (thr + mult - 1) / mult;
+    int ps = (Tp - 1) >> 1;
     if (ps > n - 1) ps = n - 1;
     int gc = (int)grp[ps];
     if (gc < g0 + 1) gc = g0 + 1;
     if (gc >= G) break;
-    if ((long long)gs[gc] + (long long)gs[gc + 1] < Tp) {
+    if ((int)gs[gc] + (int)gs[gc + 1] < Tp) {
       ++gc;
       if (gc >= G) break;
     }
@@ -232,6 +233,15 @@ struct SmallPlan {
   int off_L, off_warps, warp_smem;
   int off_W, off_A, off_Ecol, off_scb, off_cum, off_V, off_Va, off_I, off_cuts;
   int LW;     // row stride of the W / A tables (levels 0..xmax)
+  int LE;     // length of one entropy column buffer (two are kept)
+  int total;
+};
+
+// Shared-memory layout of the level-major DP kernel (byte offsets).
+struct MidPlan {
+  int off_E, off_R, off_L, off_scb, off_cum, off_I, off_cuts, off_ecol;
+  int KS;     // row stride of the level-major R table (t = 0..kmax)
+  int xmax;
   int total;
 };
 

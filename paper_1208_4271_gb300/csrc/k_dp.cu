@@ -57,7 +57,22 @@ __device__ __forceinline__ real entropy_term(const real* __restrict__ Lt, const 
                                              const int* __restrict__ cum, int ks, int yhat, int s,
                                              int t) {
   real e = Lt[scb[t] - scb[s]];
-  for (int r = 0; r < yhat; ++r) e -= Lt[cum[r * ks + t] - cum[r * ks + s]];
+  const int* __restrict__ ct = cum + t;
+  const int* __restrict__ cs = cum + s;
+  int r = 0;
+  // four rows at a time: the loads run ahead, the subtractions keep the
+  // order of increasing r
+  for (; r + 4 <= yhat; r += 4) {
+    const real l0 = Lt[ct[(r + 0) * ks] - cs[(r + 0) * ks]];
+    const real l1 = Lt[ct[(r + 1) * ks] - cs[(r + 1) * ks]];
+    const real l2 = Lt[ct[(r + 2) * ks] - cs[(r + 2) * ks]];
+    const real l3 = Lt[ct[(r + 3) * ks] - cs[(r + 3) * ks]];
+    e -= l0;
+    e -= l1;
+    e -= l2;
+    e -= l3;
+  }
+  for (; r < yhat; ++r) e -= Lt[ct[r * ks] - cs[r * ks]];
   return e;
 }
 
@@ -66,7 +81,22 @@ __device__ __forceinline__ double entropy_term64g(const double* __restrict__ L64
                                                   const int* __restrict__ cum, int ks, int yhat,
                                                   int s, int t) {
   double e = L64[scb[t] - scb[s]];
-  for (int r = 0; r < yhat; ++r) e -= L64[cum[r * ks + t] - cum[r * ks + s]];
+  const int* __restrict__ ct = cum + t;
+  const int* __restrict__ cs = cum + s;
+  int r = 0;
+  // four rows at a time: the loads run ahead, the subtractions keep the
+  // order of increasing r
+  for (; r + 4 <= yhat; r += 4) {
+    const double l0 = L64[ct[(r + 0) * ks] - cs[(r + 0) * ks]];
+    const double l1 = L64[ct[(r + 1) * ks] - cs[(r + 1) * ks]];
+    const double l2 = L64[ct[(r + 2) * ks] - cs[(r + 2) * ks]];
+    const double l3 = L64[ct[(r + 3) * ks] - cs[(r + 3) * ks]];
+    e -= l0;
+    e -= l1;
+    e -= l2;
+    e -= l3;
+  }
+  for (; r < yhat; ++r) e -= L64[ct[r * ks] - cs[r * ks]];
   return e;
 }
 

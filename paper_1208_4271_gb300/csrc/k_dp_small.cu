@@ -29,7 +29,22 @@ template <typename real>
 __device__ __forceinline__ real E_small(const real* __restrict__ Lt, const int* __restrict__ scb,
                                         const int* __restrict__ cum, int ks, int yhat, int s, int t) {
   real e = Lt[scb[t] - scb[s]];
-  for (int r = 0; r < yhat; ++r) e -= Lt[cum[r * ks + t] - cum[r * ks + s]];
+  const int* __restrict__ ct = cum + t;
+  const int* __restrict__ cs = cum + s;
+  int r = 0;
+  // four rows at a time: the loads run ahead, the subtractions keep the
+  // order of increasing r
+  for (; r + 4 <= yhat; r += 4) {
+    const real l0 = Lt[ct[(r + 0) * ks] - cs[(r + 0) * ks]];
+    const real l1 = Lt[ct[(r + 1) * ks] - cs[(r + 1) * ks]];
+    const real l2 = Lt[ct[(r + 2) * ks] - cs[(r + 2) * ks]];
+    const real l3 = Lt[ct[(r + 3) * ks] - cs[(r + 3) * ks]];
+    e -= l0;
+    e -= l1;
+    e -= l2;
+    e -= l3;
+  }
+  for (; r < yhat; ++r) e -= Lt[ct[r * ks] - cs[r * ks]];
   return e;
 }
 
@@ -103,15 +118,24 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
       const int li = lane / Pph;
       const int ph = lane - li * Pph;
       const int lv = 2 + li;  // this lane's level
+      // entropy columns double-buffered: column t+1 is formed before the
+      // levels of t are reduced, so its loads overlap that work
+      real* const Ec0 = Ecol;
+      real* const Ec1 = Ecol + S.LE;
+      if (lane == 0) Ec1[0] = E_small<real>(Lt, scb, cum, ks, yhat, 0, 1);
+      __syncwarp();
       for (int t = 1; t <= k; ++t) {
-        for (int s = lane; s < t; s += 32) Ecol[s] = E_small<real>(Lt, scb, cum, ks, yhat, s, t);
-        __syncwarp();
+        const real* Et = (t & 1) ? Ec1 : Ec0;
+        if (t < k) {
+          real* En = (t & 1) ? Ec0 : Ec1;
+          for (int s = lane; s <= t; s += 32) En[s] = E_small<real>(Lt, scb, cum, ks, yhat, s, t + 1);
+        }
         const int lt = min(t, lmax);
         real best = NINF;
         int arg = 0x7fffffff;
         if (lv <= lt) {
           for (int s = lv - 1 + ph; s < t; s += Pph) {
-            const real v = W[s * LW + (lv - 1)] - Ecol[s];
+            const real v = W[s * LW + (lv - 1)] - Et[s];
             if (v > best) {
               best = v;
               arg = s;
@@ -132,17 +156,20 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
         }
         __syncwarp();
         if (lane == 0) {
-          W[t * LW + 1] = -Ecol[0];
+          real cur = -Et[0];  // W(t,1)
+          W[t * LW + 1] = cur;
           A[t * LW + 1] = 0;
           for (int l = 2; l <= lt; ++l) {
-            const real c = W[t * LW + (l - 1)];  // s = t: W(t,l-1) - E(t,t)
-            if (c > Vb[l]) {
-              W[t * LW + l] = c;
-              A[t * LW + l] = (int16_t)t;
+            const real v = Vb[l];
+            int a;
+            if (cur > v) {  // s = t: W(t,l-1) - E(t,t) is the larger
+              a = t;
             } else {
-              W[t * LW + l] = Vb[l];
-              A[t * LW + l] = (int16_t)Va[l];
+              cur = v;
+              a = Va[l];
             }
+            W[t * LW + l] = cur;
+            A[t * LW + l] = (int16_t)a;
           }
         }
         __syncwarp();

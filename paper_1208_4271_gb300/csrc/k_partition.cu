@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
   uint16_t* gU = reinterpret_cast<uint16_t*>(sm + P.off_gU);   // [n] U position -> tie group
   unsigned char* my = sm + P.off_warps + (int64_t)wib * P.warp_smem;
   uint16_t* Qs = reinterpret_cast<uint16_t*>(my + P.off_Qs);     // V position -> row
-  int* cnt = reinterpret_cast<int*>(my + P.off_Qs);              // (aliases Qs)
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(my + P.off_Qs);    // counts (aliases Qs)
   uint16_t* q = reinterpret_cast<uint16_t*>(my + P.off_q);       // U position -> row
   uint16_t* cgrp = reinterpret_cast<uint16_t*>(my + P.off_cgrp); // U position -> clump
   uint16_t* cstart = reinterpret_cast<uint16_t*>(my + P.off_cstart);
@@ -141,21 +141,23 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       }
       const int ks = k + 1;
       __syncwarp();
-      for (int i = lane; i < yhat * ks; i += 32) cnt[i] = 0;  // Qs is dead now
+      // superclump of every clump (cstart is free once the superclumps are
+      // known): a clump lies inside one superclump
+      uint16_t* sc_of = cstart;
+      if (superclump) {
+        for (int t = lane; t < k; t += 32) {
+          const int c0 = cgrp[scb[t]], c1 = cgrp[scb[t + 1] - 1];
+          for (int c = c0; c <= c1; ++c) sc_of[c] = (uint16_t)t;
+        }
+      }
+      // counts, 16 bits each (n < 65536), two per 32-bit word
+      for (int i = lane; i < (yhat * ks + 1) / 2; i += 32) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
       __syncwarp();
       for (int m = lane; m < n; m += 32) {
-        int t;
-        if (superclump) {
-          int lo = 0, hi = k;  // largest t with scb[t] <= m
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if ((int)scb[mid] <= m) lo = mid; else hi = mid;
-          }
-          t = lo;
-        } else {
-          t = cgrp[m];
-        }
-        atomicAdd(&cnt[(int)q[m] * ks + t + 1], 1);
+        const int c = cgrp[m];
+        const int t = superclump ? (int)sc_of[c] : c;
+        const int i = (int)q[m] * ks + t + 1;
+        atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (i >> 1), 1u << (16 * (i & 1)));
       }
       __syncwarp();
       // prefix over superclumps, written to the record; row totals give H(Q)

@@ -37,6 +37,10 @@ cudaError_t dp_configure(bool fp32, bool rsm, int lev, int smem, int threads, in
 cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int smem,
                       cudaStream_t st, const DPParams& P, const DPPlan& S);
 
+cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_sm, bool set_attr);
+cudaError_t dp_mid_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
+                          const DPParams& P, const MidPlan& S);
+
 // Records a CUDA error for gmine_strerror (host code outside gmine_api.cu).
 void note_cuda_error(cudaError_t e);
 
