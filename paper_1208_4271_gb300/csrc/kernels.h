@@ -27,7 +27,7 @@ __global__ void k_rank_export(RankData rk, int64_t p, int32_t* rank_out,
 __global__ void k_equi_export(RankData rk, EquiData eq, int64_t p, int y,
                               int32_t* Q_out, int32_t* yhat_out);
 
-// the DP kernel templates are instantiated and launched in k_dp.cu only
+// each DP kernel template is instantiated and launched in its own unit
 int dp_level_group(bool fp32, int nlev);
 cudaError_t dp_small_configure(bool fp32, int smem, int threads, int* blocks_per_sm);
 cudaError_t dp_small_occupancy(bool fp32, int smem, int threads, int* blocks_per_sm);
@@ -36,6 +36,17 @@ cudaError_t dp_small_launch(bool fp32, int grid, int threads, int smem, cudaStre
 cudaError_t dp_configure(bool fp32, bool rsm, int lev, int smem, int threads, int* blocks_per_sm);
 cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int smem,
                       cudaStream_t st, const DPParams& P, const DPPlan& S);
+// one pair per instance set (k_dp_{f32,f64}_{smem,global}.cu); dp_configure
+// and dp_launch dispatch to them
+#define GM_DP_DECLARE(NAME)                                                            \
+  cudaError_t NAME##_configure(int lev, int smem, int threads, int* blocks_per_sm);     \
+  cudaError_t NAME##_launch(int lev, int grid, int threads, int smem, cudaStream_t st,  \
+                            const DPParams& P, const DPPlan& S);
+GM_DP_DECLARE(dp_f32_smem)
+GM_DP_DECLARE(dp_f32_global)
+GM_DP_DECLARE(dp_f64_smem)
+GM_DP_DECLARE(dp_f64_global)
+#undef GM_DP_DECLARE
 
 cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_sm, bool set_attr);
 cudaError_t dp_mid_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
