@@ -69,6 +69,7 @@ int device_info(DeviceInfo* d) {
 // n samples and parameters (B, c).
 struct TaskBounds {
   int B, R, xmax, kmax, cum_max, lmax;
+  int sd_max;  // ints of the s-major superclump rows: max (k+1) * SW(y), yhat <= y
 };
 
 TaskBounds task_bounds(int n, int B, double c, int ylo, int yhi) {
@@ -82,6 +83,7 @@ TaskBounds task_bounds(int n, int B, double c, int ylo, int yhi) {
     tb.kmax = std::max(tb.kmax, kk);
     tb.cum_max = std::max(tb.cum_max, y * (kk + 1));
     tb.lmax = std::max(tb.lmax, std::min(x, kk));
+    tb.sd_max = std::max(tb.sd_max, (kk + 1) * ((y + 1 + 3) & ~3));
   }
   return tb;
 }
@@ -94,24 +96,24 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   const int NW = threads / 32;
   DPPlan S{};
   S.LS = std::max(4, (tb.lmax - 1 + 3) & ~3);
-  S.LX = std::max(4, (tb.lmax + 3) & ~3);
+  S.LX = std::max(4, (tb.lmax + 3) & ~3) | 1;
   S.xmax = std::max(tb.xmax, 2);
   const int64_t rbytes = (int64_t)(tb.kmax + 1) * S.LS * rs;
   const int64_t lbytes = (int64_t)(n + 1) * rs;
   // traceback scratch aliased on the X buffers once the DP is done
-  const int64_t cuts_b = (4LL * NW * S.xmax + 15) & ~int64_t(15);
+  // (cuts of four paths per warp, I(l), l*(l))
+  const int64_t cuts_b = (4LL * 4 * NW * S.xmax + 15) & ~int64_t(15);
   const int64_t I_b = (8LL * (S.xmax + 1) + 15) & ~int64_t(15);
-  const int64_t ecol_b = 8LL * NW * (S.xmax + 1);
+  const int64_t lst_b = 4LL * (S.xmax + 1);
   S.off_I_rel = (int)cuts_b;
-  S.off_ecol_rel = (int)(cuts_b + I_b);
-  const int64_t xbytes = std::max<int64_t>((int64_t)2 * 32 * S.LX * rs, cuts_b + I_b + ecol_b);
+  S.off_lst_rel = (int)(cuts_b + I_b);
+  const int64_t xbytes = std::max<int64_t>((int64_t)2 * 32 * S.LX * rs, cuts_b + I_b + lst_b);
   int64_t fixed = 0;
   auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
   S.off_X = add(xbytes);
   S.off_Eb = add((int64_t)32 * 33 * rs);
   S.off_Rtop = add((int64_t)(tb.kmax + 1) * rs);
-  S.off_scb = add(4LL * (tb.kmax + 1));
-  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
+  S.off_sd = add(4LL * std::max(tb.sd_max, 4));
   const int reserve = 1024;
   const bool in_smem = fixed + rbytes + lbytes + 32 + reserve <= smem_optin;
   *r_in_smem = in_smem;

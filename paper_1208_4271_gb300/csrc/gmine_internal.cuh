@@ -247,10 +247,11 @@ struct MidPlan {
 
 // Shared-memory layout of the DP kernel (byte offsets).
 struct DPPlan {
-  int off_R, off_Rtop, off_X, off_Eb, off_L, off_scb, off_cum;
-  int off_I_rel, off_ecol_rel;  // traceback scratch inside the X region
+  int off_R, off_Rtop, off_X, off_Eb, off_L, off_sd;
+  int off_I_rel, off_lst_rel;  // traceback scratch inside the X region
   int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4
-  int LX;     // row stride of the X buffers: levels 1..lmax, multiple of 4
+  int LX;     // row stride of the X buffers: levels 1..lmax, odd (the lanes'
+              // rows then start in distinct shared-memory banks)
   int xmax;   // largest x of the launch
   int total;
 };

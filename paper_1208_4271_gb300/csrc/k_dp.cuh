@@ -54,69 +54,111 @@ struct Bits<double> {
   __device__ static double max(double a, double b) { return fmax(a, b); }
 };
 
+// The superclump data of a task in shared memory, s-major: row s holds
+// sd[s*SW] = c_s (the sorted position where superclump s ends) and
+// sd[s*SW + 1 + r] = cum[r][s] for the yhat rows r, SW = yhat + 1 rounded up
+// to a multiple of 4 (so that a row is whole 16-byte words).
+__host__ __device__ __forceinline__ int sd_width(int yhat) { return (yhat + 1 + 3) & ~3; }
+
 // E(s,t) = L(c_t - c_s) - sum_r L(cum[r][t] - cum[r][s]), increasing r
-template <typename real>
-__device__ __forceinline__ real entropy_term(const real* __restrict__ Lt, const int* __restrict__ scb,
-                                             const int* __restrict__ cum, int ks, int yhat, int s,
-                                             int t) {
-  real e = Lt[scb[t] - scb[s]];
-  const int* __restrict__ ct = cum + t;
-  const int* __restrict__ cs = cum + s;
-  int r = 0;
+template <typename real, typename LT>
+__device__ __forceinline__ real entropy_term(const LT* __restrict__ Lt, const int* __restrict__ sd,
+                                             int SW, int yhat, int s, int t) {
+  const int* __restrict__ ct = sd + t * SW;
+  const int* __restrict__ cs = sd + s * SW;
+  real e = (real)Lt[ct[0] - cs[0]];
+  int r = 1;
   // four rows at a time: the loads run ahead, the subtractions keep the
   // order of increasing r
-  for (; r + 4 <= yhat; r += 4) {
-    const real l0 = Lt[ct[(r + 0) * ks] - cs[(r + 0) * ks]];
-    const real l1 = Lt[ct[(r + 1) * ks] - cs[(r + 1) * ks]];
-    const real l2 = Lt[ct[(r + 2) * ks] - cs[(r + 2) * ks]];
-    const real l3 = Lt[ct[(r + 3) * ks] - cs[(r + 3) * ks]];
+  for (; r + 3 <= yhat; r += 4) {
+    const real l0 = Lt[ct[r + 0] - cs[r + 0]];
+    const real l1 = Lt[ct[r + 1] - cs[r + 1]];
+    const real l2 = Lt[ct[r + 2] - cs[r + 2]];
+    const real l3 = Lt[ct[r + 3] - cs[r + 3]];
     e -= l0;
     e -= l1;
     e -= l2;
     e -= l3;
   }
-  for (; r < yhat; ++r) e -= Lt[ct[r * ks] - cs[r * ks]];
+  for (; r <= yhat; ++r) e -= (real)Lt[ct[r] - cs[r]];
   return e;
 }
 
-__device__ __forceinline__ double entropy_term64g(const double* __restrict__ L64,
-                                                  const int* __restrict__ scb,
-                                                  const int* __restrict__ cum, int ks, int yhat,
-                                                  int s, int t) {
-  double e = L64[scb[t] - scb[s]];
-  const int* __restrict__ ct = cum + t;
-  const int* __restrict__ cs = cum + s;
-  int r = 0;
-  // four rows at a time: the loads run ahead, the subtractions keep the
-  // order of increasing r
-  for (; r + 4 <= yhat; r += 4) {
-    const double l0 = L64[ct[(r + 0) * ks] - cs[(r + 0) * ks]];
-    const double l1 = L64[ct[(r + 1) * ks] - cs[(r + 1) * ks]];
-    const double l2 = L64[ct[(r + 2) * ks] - cs[(r + 2) * ks]];
-    const double l3 = L64[ct[(r + 3) * ks] - cs[(r + 3) * ks]];
-    e -= l0;
-    e -= l1;
-    e -= l2;
-    e -= l3;
+// The same E(s,t) for a fixed t whose row td (yhat <= 7) sits in registers:
+// row s comes in one or two 16-byte broadcast loads.
+template <typename real>
+__device__ __forceinline__ real entropy_reg(const real* __restrict__ Lt, const int* __restrict__ sd,
+                                            int SW, int yhat, const int (&td)[8], int s) {
+  const int4 a = *reinterpret_cast<const int4*>(sd + s * SW);
+  real e = Lt[td[0] - a.x];
+  if (yhat > 0) e -= Lt[td[1] - a.y];
+  if (yhat > 1) e -= Lt[td[2] - a.z];
+  if (yhat > 2) e -= Lt[td[3] - a.w];
+  if (yhat > 3) {
+    const int4 b = *reinterpret_cast<const int4*>(sd + s * SW + 4);
+    e -= Lt[td[4] - b.x];
+    if (yhat > 4) e -= Lt[td[5] - b.y];
+    if (yhat > 5) e -= Lt[td[6] - b.z];
+    if (yhat > 6) e -= Lt[td[7] - b.w];
   }
-  for (; r < yhat; ++r) e -= L64[ct[r * ks] - cs[r * ks]];
   return e;
 }
+
+// max(a, b, c) in one instruction (three-operand max.f32 of sm_100 and later)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ double fmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
 // Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels
-// l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.
-template <typename real, int LEV>
+// l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.  Two s
+// per iteration: each level takes both candidates in one three-operand max,
+// and the E pair of the next iteration is formed meanwhile.
+template <typename real, int LEV, bool REG>
 __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
                                            int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
-                                           const int* __restrict__ scb, const int* __restrict__ cum,
-                                           int ks, int yhat, int tt) {
+                                           const int* __restrict__ sd, int SW, int yhat,
+                                           const int (&td)[8], int tt) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
-  // E(s+1, t) is computed while the candidates of s are formed
-  real e = entropy_term<real>(Lt, scb, cum, ks, yhat, s_lo, tt);
+  auto E = [&](int s) -> real {
+    if constexpr (REG) return entropy_reg<real>(Lt, sd, SW, yhat, td, s);
+    else return entropy_term<real>(Lt, sd, SW, yhat, s, tt);
+  };
+  int s = s_lo;
+  if (s < s_hi) {
+    real e0 = E(s), e1 = E(s + 1);
 #pragma unroll 1
-  for (int s = s_lo; s <= s_hi; ++s) {
-    const real en = s < s_hi ? entropy_term<real>(Lt, scb, cum, ks, yhat, s + 1, tt) : e;
+    for (; s + 1 <= s_hi; s += 2) {
+      const bool more = s + 3 <= s_hi;
+      const real n0 = more ? E(s + 2) : e0;
+      const real n1 = more ? E(s + 3) : e1;
+      const real* R0 = Rt + s * LS + (lc - 2);
+      const real* R1 = R0 + LS;
+#pragma unroll
+      for (int g = 0; g < LEV / VW; ++g) {
+        if constexpr (sizeof(real) == 4) {
+          const float4 a = *reinterpret_cast<const float4*>(R0 + 4 * g);
+          const float4 b = *reinterpret_cast<const float4*>(R1 + 4 * g);
+          acc[4 * g + 0] = fmax3(acc[4 * g + 0], a.x - e0, b.x - e1);
+          acc[4 * g + 1] = fmax3(acc[4 * g + 1], a.y - e0, b.y - e1);
+          acc[4 * g + 2] = fmax3(acc[4 * g + 2], a.z - e0, b.z - e1);
+          acc[4 * g + 3] = fmax3(acc[4 * g + 3], a.w - e0, b.w - e1);
+        } else {
+          const double2 a = *reinterpret_cast<const double2*>(R0 + 2 * g);
+          const double2 b = *reinterpret_cast<const double2*>(R1 + 2 * g);
+          acc[2 * g + 0] = fmax3(acc[2 * g + 0], a.x - e0, b.x - e1);
+          acc[2 * g + 1] = fmax3(acc[2 * g + 1], a.y - e0, b.y - e1);
+        }
+      }
+      e0 = n0;
+      e1 = n1;
+    }
+  }
+  if (s == s_hi) {  // an odd count: the last s alone
+    const real e = E(s);
     const real* Rs = Rt + s * LS + (lc - 2);
 #pragma unroll
     for (int g = 0; g < LEV / VW; ++g) {
@@ -132,7 +174,6 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
         acc[2 * g + 1] = BT::max(acc[2 * g + 1], r.y - e);
       }
     }
-    e = en;
   }
 }
 
@@ -150,7 +191,7 @@ __device__ __forceinline__ void flush(const real (&acc)[LEV], typename Bits<real
 template <typename real, int LEV>
 __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int lmax, int s_begin, int s_end,
                         bool stealing, int* s_next, const real* __restrict__ Lt,
-                        const int* __restrict__ scb, const int* __restrict__ cum, int ks, int yhat,
+                        const int* __restrict__ sd, int SW, int yhat,
                         int tt, bool tv, typename Bits<real>::U* Xrow, int warp, int NW, int lane) {
   using BT = Bits<real>;
   const int CH = stealing ? 8 : 4;  // s per grab
@@ -158,6 +199,11 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
   const int npass = (nlev + LEV - 1) / LEV;
   const int nsb = (s_end - s_begin + CH - 1) / CH;  // s-chunks per pass
   if (nsb <= 0) return;
+  // this lane's row t in registers when it is short
+  const bool reg = yhat <= 7;
+  int td[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) td[c] = (reg && c < SW) ? sd[tt * SW + c] : 0;
   real acc[LEV];
   int cur_pass = -1;
   int g = stealing ? 0 : warp;
@@ -178,7 +224,10 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
     }
     const int s_lo = s_begin + sb * CH;
     const int s_hi = min(s_end - 1, s_lo + CH - 1);
-    accumulate<real, LEV>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, scb, cum, ks, yhat, tt);
+    if (reg)
+      accumulate<real, LEV, true>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+    else
+      accumulate<real, LEV, false>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
     if (!stealing) g += NW;
   }
   if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
@@ -248,12 +297,10 @@ k_dp(DPParams P, DPPlan S) {
   real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // [kmax+1]
   U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // [32][33]
-  int* scb = reinterpret_cast<int*>(sm + S.off_scb);      // [kmax+1]
-  int* cum = reinterpret_cast<int*>(sm + S.off_cum);      // [cum_max]
+  int* sd = reinterpret_cast<int*>(sm + S.off_sd);        // [kmax+1][SW]
   // after the DP the X buffers hold the traceback scratch
-  int* cuts = reinterpret_cast<int*>(sm + S.off_X);                       // [NW][xmax]
+  int* cuts = reinterpret_cast<int*>(sm + S.off_X);                       // [4 NW][xmax]
   double* Iw = reinterpret_cast<double*>(sm + S.off_X + S.off_I_rel);     // [xmax+1]
-  double* Ecw = reinterpret_cast<double*>(sm + S.off_X + S.off_ecol_rel);  // [NW][xmax+1]
   const int LS = S.LS;
   const int LX = S.LX;
   const real* Lt;  // L(m) = m ln m, m = 0..n
@@ -300,8 +347,12 @@ k_dp(DPParams P, DPPlan S) {
     const int x = B / y;
     const int ks = k + 1;
     const int lmax = min(x, k);
-    for (int j = tid; j <= k; j += T) scb[j] = rec[6 + j];
-    for (int i = tid; i < yhat * ks; i += T) cum[i] = rec[6 + ks + i];
+    const int SW = sd_width(yhat);
+    // record (ends, then cum row-major) -> s-major rows; unused columns 0
+    for (int i = tid; i < SW * ks; i += T) {
+      const int c = i / ks, j = i - c * ks;
+      sd[j * SW + c] = c <= yhat ? rec[6 + c * ks + j] : 0;
+    }
     if (P.trace.d_sc_ends && ks <= P.trace.sc_stride)
       for (int j = tid; j <= k; j += T) P.trace.d_sc_ends[trace_task * P.trace.sc_stride + j] = rec[6 + j];
     __syncthreads();
@@ -314,12 +365,12 @@ k_dp(DPParams P, DPPlan S) {
       for (int i = tid; i < 2 * 32 * LX; i += T) Xb[i] = NINF_BITS;
       __syncthreads();
       for (int t = 1 + tid; t <= k; t += T) {
-        const real r1 = -entropy_term<real>(Lt, scb, cum, ks, yhat, 0, t);
+        const real r1 = -entropy_term<real>(Lt, sd, SW, yhat, 0, t);
         if (lmax == 1) Rtop[t] = r1; else Rt[t * LS] = r1;
       }
       for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block 0
         const int i = idx >> 5, j = idx & 31;
-        if (i < j && 1 + j <= k) Eb[i * 33 + j] = entropy_term<real>(Lt, scb, cum, ks, yhat, 1 + i, 1 + j);
+        if (i < j && 1 + j <= k) Eb[i * 33 + j] = entropy_term<real>(Lt, sd, SW, yhat, 1 + i, 1 + j);
       }
       if (tid == 0) s_next = 0;
       __syncthreads();
@@ -390,7 +441,7 @@ k_dp(DPParams P, DPPlan S) {
           const int sb0 = stealing ? 1 : t0;
           const int sb1 = stealing ? t0 : t1;
           if (next && sb1 > sb0)
-            phase_a<real, LEV>(Rt, LS, lmax, sb0, sb1, stealing, &s_next, Lt, scb, cum, ks, yhat, ttn,
+            phase_a<real, LEV>(Rt, LS, lmax, sb0, sb1, stealing, &s_next, Lt, sd, SW, yhat, ttn,
                                tnv, Xnxt + lane * LX, warp, NW, lane);
           if (step == 1) {
             for (int i = tid; i < 32 * LX; i += T) Xcur[i] = NINF_BITS;  // for block b+2
@@ -399,7 +450,7 @@ k_dp(DPParams P, DPPlan S) {
               for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block b+1
                 const int i = idx >> 5, j = idx & 31;
                 if (i < j && t1 + j <= k)
-                  Eb[i * 33 + j] = entropy_term<real>(Lt, scb, cum, ks, yhat, t1 + i, t1 + j);
+                  Eb[i * 33 + j] = entropy_term<real>(Lt, sd, SW, yhat, t1 + i, t1 + j);
               }
           }
           __syncthreads();
@@ -412,57 +463,93 @@ k_dp(DPParams P, DPPlan S) {
     if (k >= 2 && need_paths) {
       int* mycut = cuts + warp * S.xmax;
       if constexpr (fp32) {
-        // Traceback in the R recursion: l* = the level of the largest R(k, l'),
-        // l' <= l (first in increasing l'), then at (t, lv) an s with
-        // R(s, lv-1) - E(s, t) equal to R(t, lv) (an exact match exists: a
-        // maximum is one of its candidates).  The scan runs down from t - 1,
-        // so it covers about one column; since E >= 0, an s with R(s, lv-1)
-        // below the target cannot match and its E is not formed.
-        for (int l = 2 + warp; l <= lmax; l += NW) {
-          int lstar = 1;
-          real best = Rget(k, 1);
-          for (int lv = 2; lv <= l; ++lv) {
-            const real r = Rget(k, lv);
-            if (r > best) {
-              best = r;
-              lstar = lv;
-            }
-          }
-          int tcur = k;
-          for (int lv = lstar; lv >= 2; --lv) {
-            const real target = Rget(tcur, lv);
-            int found = -1;
-            for (int s0 = tcur - 1; s0 >= lv - 1 && found < 0; s0 -= 32) {
-              const int s = s0 - lane;
-              bool hit = false;
-              if (s >= lv - 1) {
-                const real r = Rt[s * LS + (lv - 2)];
-                if (r >= target) hit = r - entropy_term<real>(Lt, scb, cum, ks, yhat, s, tcur) == target;
+        // Traceback in the R recursion.  l*(l) = the level of the largest
+        // R(k, l'), l' <= l (the first in increasing l'), from one warp scan;
+        // then from (k, l*) at (t, lv) an s with R(s, lv-1) - E(s, t) equal
+        // to R(t, lv) (an exact match exists: a maximum is one of its
+        // candidates), scanning down from t - 1.  Since E >= 0, an s with
+        // R(s, lv-1) below the target cannot match and its E is not formed.
+        // Each warp follows four paths at once, one per group of 8 lanes,
+        // largest l first; every path is then re-scored in double.
+        int* lst = reinterpret_cast<int*>(sm + S.off_X + S.off_lst_rel);
+        if (warp == 0) {
+          real cbest = Rget(k, 1);
+          int carg = 1;
+          for (int l0 = 2; l0 <= lmax; l0 += 32) {
+            const int l = l0 + lane;
+            real v = l <= lmax ? Rget(k, l) : NINF;
+            int a = l;
+            // inclusive scan over levels: a later level wins only when larger
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const real ov = __shfl_up_sync(0xffffffffu, v, d);
+              const int oa = __shfl_up_sync(0xffffffffu, a, d);
+              if (lane >= d && !(v > ov)) {
+                v = ov;
+                a = oa;
               }
-              const unsigned m = __ballot_sync(0xffffffffu, hit);
-              if (m) found = s0 - (__ffs(m) - 1);
             }
-            if (found < 0) found = lv - 1;  // unreachable: R(t,lv) is one of its candidates
-            if (lane == 0) mycut[lv - 2] = found;
-            tcur = found;
+            if (!(v > cbest)) {  // the levels before l0
+              v = cbest;
+              a = carg;
+            }
+            if (l <= lmax) lst[l] = a;
+            cbest = __shfl_sync(0xffffffffu, v, 31);
+            carg = __shfl_sync(0xffffffffu, a, 31);
+          }
+        }
+        __syncthreads();
+        const int grp = lane >> 3, sub = lane & 7;
+        int* gcut = cuts + (warp * 4 + grp) * S.xmax;
+        const int npaths = lmax - 1;  // levels 2..lmax
+        for (int base = warp * 4; base < npaths; base += NW * 4) {
+          const int pidx = base + grp;
+          const bool act = pidx < npaths;  // the same in the whole group
+          const int l = lmax - pidx;
+          const int lstar = act ? lst[l] : 1;
+          int lv = lstar, tcur = k, s0 = k - 1;
+          bool going = act && lv >= 2;
+          real target = going ? Rget(k, lv) : NINF;
+          while (__any_sync(0xffffffffu, going)) {
+            const int s = s0 - sub;
+            bool hit = false;
+            if (going && s >= lv - 1) {
+              const real r = Rt[s * LS + (lv - 2)];
+              if (r >= target) hit = r - entropy_term<real>(Lt, sd, SW, yhat, s, tcur) == target;
+            }
+            const unsigned m = (__ballot_sync(0xffffffffu, hit) >> (8 * grp)) & 0xffu;
+            if (going) {
+              int found = -1;
+              if (m) found = s0 - (__ffs(m) - 1);
+              else if (s0 - 8 < lv - 1) found = lv - 1;  // unreachable: R(t,lv) is a candidate
+              if (found >= 0) {
+                if (sub == 0) gcut[lv - 2] = found;
+                tcur = found;
+                --lv;
+                s0 = tcur - 1;
+                if (lv >= 2) target = Rget(tcur, lv); else going = false;
+              } else {
+                s0 -= 8;
+              }
+            }
           }
           __syncwarp();
-          // re-score the chosen partition in double, in the DP's own order:
-          // w = -E(0,s_1) - E(s_1,s_2) - ... - E(s_{l*-1},k)
-          double* ec = Ecw + warp * (S.xmax + 1);
-          for (int c = lane; c < lstar; c += 32) {
-            const int a = c == 0 ? 0 : mycut[c - 1];
-            const int bnd = c == lstar - 1 ? k : mycut[c];
-            ec[c] = entropy_term64g(P.L64, scb, cum, ks, yhat, a, bnd);
-          }
-          __syncwarp();
-          double w = -ec[0];
-          for (int c = 1; c < lstar; ++c) w = w - ec[c];
-          if (lane == 0) Iw[l] = HQ + w / (double)n;
-          if (P.trace.d_cuts) {
+          // -E(0,s_1) - E(s_1,s_2) - ... - E(s_{l*-1},k) in double
+          double part = 0.0;
+          if (act)
+            for (int c = sub; c < lstar; c += 8) {
+              const int a = c == 0 ? 0 : gcut[c - 1];
+              const int bnd = c == lstar - 1 ? k : gcut[c];
+              part -= entropy_term<double>(P.L64, sd, SW, yhat, a, bnd);
+            }
+          part += __shfl_xor_sync(0xffffffffu, part, 4);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          if (act && sub == 0) Iw[l] = HQ + part / (double)n;
+          if (act && P.trace.d_cuts) {
             // as l - 1 column ends: the l* - 1 cuts, then empty columns at k
             int32_t* dst = P.trace.d_cuts + trace_task * P.trace.cut_stride + (l - 2) * (l - 1) / 2;
-            for (int c = lane; c < l - 1; c += 32) dst[c] = c < lstar - 1 ? mycut[c] : k;
+            for (int c = sub; c < l - 1; c += 8) dst[c] = c < lstar - 1 ? gcut[c] : k;
           }
           __syncwarp();
         }
@@ -486,7 +573,7 @@ k_dp(DPParams P, DPPlan S) {
             int arg = 0x7fffffff;
             for (int s = lv - 1 + lane; s <= tcur; s += 32) {
               const real wv = Rt[s * LS + (lv - 2)];
-              const real cand = (s == tcur) ? wv : wv - entropy_term<real>(Lt, scb, cum, ks, yhat, s, tcur);
+              const real cand = (s == tcur) ? wv : wv - entropy_term<real>(Lt, sd, SW, yhat, s, tcur);
               if (cand > best) {
                 best = cand;
                 arg = s;
