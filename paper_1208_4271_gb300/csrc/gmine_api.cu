@@ -69,7 +69,8 @@ int device_info(DeviceInfo* d) {
 // n samples and parameters (B, c).
 struct TaskBounds {
   int B, R, xmax, kmax, cum_max, lmax;
-  int sd_max;  // ints of the s-major superclump rows: max (k+1) * SW(y), yhat <= y
+  int sd_max;   // ints of the s-major superclump rows: max (k+1) * SW(y), yhat <= y
+  int rec_max;  // ints of the largest task record
 };
 
 TaskBounds task_bounds(int n, int B, double c, int ylo, int yhi) {
@@ -84,6 +85,7 @@ TaskBounds task_bounds(int n, int B, double c, int ylo, int yhi) {
     tb.cum_max = std::max(tb.cum_max, y * (kk + 1));
     tb.lmax = std::max(tb.lmax, std::min(x, kk));
     tb.sd_max = std::max(tb.sd_max, (kk + 1) * ((y + 1 + 3) & ~3));
+    tb.rec_max = std::max(tb.rec_max, (6 + (kk + 1) * (y + 1) + 3) & ~3);
   }
   return tb;
 }
@@ -169,14 +171,10 @@ SmallPlan make_small_plan(int n, const TaskBounds& tb, bool fp32, int warps) {
   S.off_L = add((int64_t)(n + 1) * rs);
   S.off_warps = o;
   o = 0;
+  S.off_E = add((int64_t)tb.kmax * (tb.kmax + 1) / 2 * rs);
   S.off_W = add((int64_t)(tb.kmax + 1) * S.LW * rs);
   S.off_A = add((int64_t)(tb.kmax + 1) * S.LW * 2);
-  S.LE = (tb.kmax + 1 + 3) & ~3;
-  S.off_Ecol = add((int64_t)2 * S.LE * rs);
-  S.off_scb = add(4LL * (tb.kmax + 1));
-  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
-  S.off_V = add((int64_t)S.LW * rs);
-  S.off_Va = add(4LL * S.LW);
+  S.off_rec = add(4LL * std::max(tb.rec_max, 4));
   S.off_I = add(8LL * S.LW);
   S.off_cuts = add(4LL * S.LW * S.LW);
   S.warp_smem = o;
@@ -196,8 +194,7 @@ MidPlan make_mid_plan(int n, const TaskBounds& tb, bool fp32, int threads) {
   S.off_E = add((int64_t)tb.kmax * (tb.kmax + 1) / 2 * rs);
   S.off_R = add((int64_t)(tb.lmax + 1) * S.KS * rs);
   S.off_L = add((int64_t)(n + 1) * rs);
-  S.off_scb = add(4LL * (tb.kmax + 1));
-  S.off_cum = add(4LL * std::max(tb.cum_max, 1));
+  S.off_rec = add(4LL * std::max(tb.rec_max, 4));
   S.off_I = add(8LL * (S.xmax + 1));
   S.off_cuts = add(4LL * NW * S.xmax);
   S.off_ecol = add(8LL * NW * (S.xmax + 1));
@@ -217,6 +214,8 @@ struct DPGroup {
   bool rsm;
   bool small;      // warp-per-task kernel
   bool mid;        // level-major kernel
+  bool two;        // two-column kernel (x = 2)
+  int smem_two, off_two_rec, two_rec_bytes;
   DPPlan S;
   SmallPlan SS;
   MidPlan MS;
@@ -234,7 +233,7 @@ struct Layout {
   int part_ctas;
   int64_t rec_per_orient;
   int64_t cells_max;
-  int64_t o_Btab, o_L64, o_L32, o_lnt, o_nf;
+  int64_t o_Btab, o_L64, o_L32, o_lnt, o_recoff, o_nf;
   int64_t o_perm, o_pos, o_grp, o_gstart, o_ngroups, o_nslot;
   int64_t o_bounds, o_yhat;
   int64_t o_slot, o_nused, o_Bp, o_flags, o_dirty, o_ndirty;
@@ -307,8 +306,13 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   // DP launch groups: consecutive row counts whose x - 1 share a level group
   L->ngroups = 0;
   for (int y = 2; y <= B / 2; ++y) {
-    const int lev = dp_level_group(fp32, std::max(B / y - 1, 1));
-    if (L->ngroups > 0 && L->grp[L->ngroups - 1].lev == lev) {
+    // x = 2 (one level above the first) has a kernel of its own; row counts
+    // with few levels are grouped by x (each launch is planned for its own
+    // task sizes)
+    const int x = B / y;
+    const int lev = x == 2 ? 2 : dp_level_group(fp32, std::max(x - 1, 1));
+    if (L->ngroups > 0 && L->grp[L->ngroups - 1].lev == lev &&
+        (lev > 4 || B / L->grp[L->ngroups - 1].ylo == x)) {
       L->grp[L->ngroups - 1].yhi = y;
     } else {
       if (L->ngroups == kMaxDPGroups) return GMINE_E_LIMIT;
@@ -321,6 +325,25 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   for (int gi = 0; gi < L->ngroups; ++gi) {
     DPGroup& g = L->grp[gi];
     const TaskBounds tg = task_bounds((int)n, B, param->c, g.ylo, g.yhi);
+    if (g.lev == 2) {
+      int blocks = 0;
+      g.two = true;
+      // the L table, then one task record per warp (8 warps, fewer if
+      // shared memory is short)
+      g.off_two_rec = (int)(((n + 1) * (fp32 ? 4 : 8) + 15) & ~int64_t(15));
+      g.two_rec_bytes = (4 * std::max(tg.rec_max, 4) + 15) & ~15;
+      g.threads = 256;
+      while (g.threads > 32 && g.off_two_rec + g.threads / 32 * g.two_rec_bytes + 1024 > dev.smem_optin)
+        g.threads /= 2;
+      g.smem_two = g.off_two_rec + g.threads / 32 * g.two_rec_bytes;
+      if (g.smem_two + 1024 > dev.smem_optin) return GMINE_E_LIMIT;
+      cudaError_t e = dp_two_configure(fp32, g.smem_two, g.threads, &blocks);
+      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+      if (blocks < 1) return GMINE_E_LIMIT;
+      g.ctas = blocks * dev.sms;
+      g.scratch_per_cta = 0;
+      continue;
+    }
     if (g.lev >= 8 && g.lev <= 12) {
       // few levels, entropy triangle small enough for two CTAs per SM:
       // level-major kernel (no chain along t)
@@ -438,6 +461,7 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   L->o_L64 = take(8 * (n + 1));
   L->o_L32 = take(4 * (n + 1));
   L->o_lnt = take(8 * (n + 1));
+  L->o_recoff = take(8 * (B / 2 + 2));
   L->o_nf = take(4 * p);
   L->o_perm = take(4 * S * n);
   L->o_pos = take(4 * S * n);
@@ -525,13 +549,14 @@ int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
 }
 
 // Ranks and equipartitions of the clean variables (slots 0..p-1).
-int prepare_variables(const double* d_vars, void* ws, const Layout& L, double alpha,
+int prepare_variables(const double* d_vars, void* ws, const Layout& L, double alpha, double c,
                       cudaStream_t st, int* launches) {
   int rc = upload_Btab(ws, L, alpha, st);
   if (rc != GMINE_OK) return rc;
   const int n = (int)L.n;
-  k_tables<<<(n + 256) / 256, 256, 0, st>>>(n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32),
-                                             at<double>(ws, L.o_lnt));
+  k_tables<<<(std::max(n, L.B) + 256) / 256, 256, 0, st>>>(
+      n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32), at<double>(ws, L.o_lnt), L.B, c,
+      at<int64_t>(ws, L.o_recoff));
   GM_CUDA(cudaGetLastError());
   ++*launches;
   if (L.p > 0) {
@@ -621,7 +646,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* ws = d_workspace;
   int launches = 0;
-  rc = prepare_variables(d_vars, ws, L, param->alpha, st, &launches);
+  rc = prepare_variables(d_vars, ws, L, param->alpha, param->c, st, &launches);
   if (rc != GMINE_OK) return rc;
 
   const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
@@ -662,6 +687,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
       Q.lnt = at<double>(ws, L.o_lnt);
       Q.rec = at<int32_t>(ws, L.o_rec);
       Q.rec_per_orient = L.rec_per_orient;
+      Q.rec_off = at<int64_t>(ws, L.o_recoff);
       Q.B_full = L.B;
       Q.n_full = (int)L.n;
       Q.c = param->c;
@@ -687,6 +713,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
       P.pp = pp;
       P.rec = Q.rec;
       P.rec_per_orient = L.rec_per_orient;
+      P.rec_off = Q.rec_off;
       P.B_full = L.B;
       P.n_full = (int)L.n;
       P.c = param->c;
@@ -714,7 +741,10 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
           GM_CUDA(timing->pair(&e0, &e1));
           GM_CUDA(cudaEventRecord(e0, st));
         }
-        if (g.mid)
+        if (g.two)
+          GM_CUDA(dp_two_launch(fp32, g.ctas, g.threads, g.smem_two, st, P, g.off_two_rec,
+                                g.two_rec_bytes));
+        else if (g.mid)
           GM_CUDA(dp_mid_launch(fp32, g.ctas, g.threads, g.MS.total, st, P, g.MS));
         else if (g.small)
           GM_CUDA(dp_small_launch(fp32, g.ctas, g.threads, g.SS.total, st, P, g.SS));
@@ -797,7 +827,7 @@ int gmine_rank(const double* d_vars, int64_t p, int64_t n, int32_t* d_perm, int3
   if (p == 0 || n == 0) return GMINE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int launches = 0;
-  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st, &launches);
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, prm.c, st, &launches);
   if (rc != GMINE_OK) return rc;
   dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)p);
   k_rank_export<<<grid, 256, 0, st>>>(rank_data(d_workspace, L), p, d_rank, d_perm, d_groups);
@@ -817,7 +847,7 @@ int gmine_equipartition(const double* d_vars, int64_t p, int64_t n, int32_t y, i
   if (p == 0 || n == 0) return GMINE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int launches = 0;
-  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, st, &launches);
+  rc = prepare_variables(d_vars, d_workspace, L, prm.alpha, prm.c, st, &launches);
   if (rc != GMINE_OK) return rc;
   // one row count y for every variable: reuse the bounds rows of y = 2
   // as output space through a dedicated single-y kernel

@@ -149,6 +149,26 @@ __host__ __device__ __forceinline__ int64_t rec_offset(int B, int n, double c, i
   return off;
 }
 
+// Copies the first nint ints of a task record to shared memory with 16-byte
+// loads, four in flight per thread (threads tid, tid + T, ... of a group of
+// T).  Records start on 16-byte boundaries and are padded to a multiple of
+// 4 ints, so the rounded-up copy stays inside the record.
+__device__ __forceinline__ void copy_record(int* __restrict__ dst, const int32_t* __restrict__ src,
+                                            int nint, int tid, int T) {
+  const int n4 = (nint + 3) >> 2;
+  const int4* __restrict__ s4 = reinterpret_cast<const int4*>(src);
+  int4* __restrict__ d4 = reinterpret_cast<int4*>(dst);
+  for (int i0 = tid; i0 < n4; i0 += 4 * T) {
+    int4 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (i0 + q * T < n4) v[q] = s4[i0 + q * T];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (i0 + q * T < n4) d4[i0 + q * T] = v[q];
+  }
+}
+
 // first cell of row count y in the y-major layout of M
 __device__ __forceinline__ int row_offset(int B, int y) {
   int off = 0;
@@ -199,6 +219,7 @@ struct PartParams {
   int B_full, n_full;  // B and n of the full sample count
   double c;
   int64_t chunk_pairs;
+  const int64_t* rec_off;     // [B/2+2] first int of row count y's record
   unsigned long long* queue;  // atomic (pair, orientation) counter
   int off_pi, off_gU;  // shared by the CTA: [n] uint16 each
   int off_warps;       // first per-warp region
@@ -210,6 +231,7 @@ struct DPParams {
   PairPrep pp;
   const int32_t* rec;
   int64_t rec_per_orient;
+  const int64_t* rec_off;  // [B/2+2] first int of row count y's record
   int B_full, n_full;
   double c;
   const double* L64;
@@ -231,15 +253,14 @@ struct DPParams {
 // CTA's entropy table, then one region per warp.
 struct SmallPlan {
   int off_L, off_warps, warp_smem;
-  int off_W, off_A, off_Ecol, off_scb, off_cum, off_V, off_Va, off_I, off_cuts;
+  int off_E, off_W, off_A, off_rec, off_I, off_cuts;  // within a warp region
   int LW;     // row stride of the W / A tables (levels 0..xmax)
-  int LE;     // length of one entropy column buffer (two are kept)
   int total;
 };
 
 // Shared-memory layout of the level-major DP kernel (byte offsets).
 struct MidPlan {
-  int off_E, off_R, off_L, off_scb, off_cum, off_I, off_cuts, off_ecol;
+  int off_E, off_R, off_L, off_rec, off_I, off_cuts, off_ecol;
   int KS;     // row stride of the level-major R table (t = 0..kmax)
   int xmax;
   int total;

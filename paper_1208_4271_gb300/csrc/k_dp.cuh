@@ -332,7 +332,7 @@ k_dp(DPParams P, DPPlan S) {
     const int n = P.pp.n_used[pl];
     const int B = P.pp.B[pl];
     const int32_t* rec = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient +
-                         rec_offset(P.B_full, P.n_full, P.c, y);
+                         P.rec_off[y];
     const int64_t trace_task = ((int64_t)(y - 2) * 2 + o) * P.trace_npairs + P.trace_pair0 + pl;
     const bool valid = n >= 4 && B >= 4 && y <= B / 2;
     const int k = valid ? rec[0] : 0;

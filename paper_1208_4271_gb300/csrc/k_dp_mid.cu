@@ -81,8 +81,7 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
   real* Et = reinterpret_cast<real*>(sm + S.off_E);      // packed triangle
   real* Rl = reinterpret_cast<real*>(sm + S.off_R);      // [lmax+1][KS]: R(t,l) at l*KS+t
   real* Lt = reinterpret_cast<real*>(sm + S.off_L);      // [n+1]
-  int* scb = reinterpret_cast<int*>(sm + S.off_scb);     // [kmax+1]
-  int* cum = reinterpret_cast<int*>(sm + S.off_cum);     // [cum_max]
+  int* recb = reinterpret_cast<int*>(sm + S.off_rec);    // the task's record
   double* Iw = reinterpret_cast<double*>(sm + S.off_I);  // [xmax+1]
   int* cuts = reinterpret_cast<int*>(sm + S.off_cuts);   // [NW][xmax]
   double* Ecw = reinterpret_cast<double*>(sm + S.off_ecol);  // [NW][xmax+1]
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
     const int n = P.pp.n_used[pl];
     const int B = P.pp.B[pl];
     const int32_t* rec = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient +
-                         rec_offset(P.B_full, P.n_full, P.c, y);
+                         P.rec_off[y];
     const int64_t trace_task = ((int64_t)(y - 2) * 2 + o) * P.trace_npairs + P.trace_pair0 + pl;
     const bool valid = n >= 4 && B >= 4 && y <= B / 2;
     const int k = valid ? rec[0] : 0;
@@ -124,8 +123,9 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
     const int x = B / y;
     const int ks = k + 1;
     const int lmax = min(x, k);
-    for (int j = tid; j <= k; j += T) scb[j] = rec[6 + j];
-    for (int i = tid; i < yhat * ks; i += T) cum[i] = rec[6 + ks + i];
+    copy_record(recb, rec, 6 + ks + yhat * ks, tid, T);
+    const int* scb = recb + 6;      // superclump ends
+    const int* cum = recb + 6 + ks;  // cum[r][t] at r * ks + t
     if (P.trace.d_sc_ends && ks <= P.trace.sc_stride)
       for (int j = tid; j <= k; j += T) P.trace.d_sc_ends[trace_task * P.trace.sc_stride + j] = rec[6 + j];
     __syncthreads();

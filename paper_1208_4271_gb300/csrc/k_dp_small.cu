@@ -1,20 +1,24 @@
 // k_dp_small.cu -- the OptimizeXAxis dynamic program for tasks with few
-// columns (x <= 9, small superclump counts), one warp per task.
+// columns (3 <= x <= 9) and few superclumps, one warp per task, level after
+// level.
 //
 // The recursion is the method's own (SOM Algorithm 2; Appendix item 10):
 //   W(t,1) = -E(0,t),  W(t,l) = max_{s in [l-1, t]} W(s,l-1) - E(s,t)
-// with s = t an empty last column (E(t,t) = 0), the first maximum in
-// increasing s chosen, computed t after t.  For each t the warp first forms
-// the entropy column E(., t) (Appendix item 10b), then every level: lanes
-// are split into (level, phase) groups, phase p scanning s = l-1+p, l-1+p+P,
-// ..., and a few shuffles combine the phases (larger value, else smaller s).
-// The argument table A(t,l) is kept, so the chosen partitions follow
-// directly.  The plain path keeps the table in double; the float path
-// re-scores each chosen partition in double.
+// with s = t an empty last column (E(t,t) = 0) and the first maximum in
+// increasing s chosen.  The warp first forms the whole entropy triangle
+// E(s,t), s < t (Appendix item 10b), every lane busy, then takes the levels
+// one after another: within a level every t is independent, lanes over t,
+// each lane scanning s upwards and keeping the argument A(t,l).  W(t,l) is
+// needed for t >= l (a source of level l+1 has s >= l) and, at the last
+// level, only at t = k: that cell is one warp-wide argmax.  The chosen
+// partitions follow from A.  The plain path keeps W in double; the float
+// path re-scores each chosen partition in double.
 #include "gmine_internal.cuh"
 #include "kernels.h"
 
 namespace gm {
+
+namespace {
 
 template <typename real>
 __device__ __forceinline__ real ninf_of();
@@ -25,6 +29,7 @@ __device__ __forceinline__ double ninf_of<double>() {
   return __longlong_as_double((long long)0xfff0000000000000ull);
 }
 
+// E(s,t) = L(c_t - c_s) - sum_r L(cum[r][t] - cum[r][s]), increasing r
 template <typename real>
 __device__ __forceinline__ real E_small(const real* __restrict__ Lt, const int* __restrict__ scb,
                                         const int* __restrict__ cum, int ks, int yhat, int s, int t) {
@@ -48,6 +53,45 @@ __device__ __forceinline__ real E_small(const real* __restrict__ Lt, const int* 
   return e;
 }
 
+// E(s1,t1) and E(s2,t2) with their loads interleaved: two independent
+// chains per lane, each in increasing r
+template <typename real>
+__device__ __forceinline__ void E_small2(const real* __restrict__ Lt, const int* __restrict__ scb,
+                                         const int* __restrict__ cum, int ks, int yhat, int s1, int t1,
+                                         int s2, int t2, real& e1, real& e2) {
+  real a = Lt[scb[t1] - scb[s1]];
+  real b = Lt[scb[t2] - scb[s2]];
+  const int* __restrict__ ct1 = cum + t1;
+  const int* __restrict__ cs1 = cum + s1;
+  const int* __restrict__ ct2 = cum + t2;
+  const int* __restrict__ cs2 = cum + s2;
+  int r = 0;
+  for (; r + 4 <= yhat; r += 4) {
+    real la[4], lb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      la[q] = Lt[ct1[(r + q) * ks] - cs1[(r + q) * ks]];
+      lb[q] = Lt[ct2[(r + q) * ks] - cs2[(r + q) * ks]];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a -= la[q];
+      b -= lb[q];
+    }
+  }
+  for (; r < yhat; ++r) {
+    a -= Lt[ct1[r * ks] - cs1[r * ks]];
+    b -= Lt[ct2[r * ks] - cs2[r * ks]];
+  }
+  e1 = a;
+  e2 = b;
+}
+
+// offset of E(s, .) in the packed triangle: row s holds t = s+1 .. k
+__device__ __forceinline__ int tri_row(int s, int k) { return s * k - (s * (s - 1)) / 2; }
+
+}  // namespace
+
 template <typename real>
 __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -56,13 +100,10 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
   const int wib = threadIdx.x >> 5;
   const int LW = S.LW;
   unsigned char* my = sm + S.off_warps + (int64_t)wib * S.warp_smem;
+  real* Et = reinterpret_cast<real*>(my + S.off_E);            // packed triangle
   real* W = reinterpret_cast<real*>(my + S.off_W);             // [kmax+1][LW]
   int16_t* A = reinterpret_cast<int16_t*>(my + S.off_A);       // [kmax+1][LW]
-  real* Ecol = reinterpret_cast<real*>(my + S.off_Ecol);       // [kmax+1]
-  int* scb = reinterpret_cast<int*>(my + S.off_scb);           // [kmax+1]
-  int* cum = reinterpret_cast<int*>(my + S.off_cum);           // [cum_max]
-  real* Vb = reinterpret_cast<real*>(my + S.off_V);            // [LW]
-  int* Va = reinterpret_cast<int*>(my + S.off_Va);             // [LW]
+  int* recb = reinterpret_cast<int*>(my + S.off_rec);          // the task's record
   double* Iw = reinterpret_cast<double*>(my + S.off_I);        // [LW]
   int* cuts = reinterpret_cast<int*>(my + S.off_cuts);         // [LW][LW]
   const real* Lt;
@@ -89,7 +130,7 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
     const int n = P.pp.n_used[pl];
     const int B = P.pp.B[pl];
     const int32_t* rec = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient +
-                         rec_offset(P.B_full, P.n_full, P.c, y);
+                         P.rec_off[y];
     const int64_t trace_task = ((int64_t)(y - 2) * 2 + o) * P.trace_npairs + P.trace_pair0 + pl;
     const bool valid = n >= 4 && B >= 4 && y <= B / 2;
     const int k = valid ? rec[0] : 0;
@@ -104,45 +145,89 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
     const int x = B / y;
     const int ks = k + 1;
     const int lmax = min(x, k);
-    for (int j = lane; j <= k; j += 32) scb[j] = rec[6 + j];
-    for (int i = lane; i < yhat * ks; i += 32) cum[i] = rec[6 + ks + i];
+    copy_record(recb, rec, 6 + ks + yhat * ks, lane, 32);
+    const int* scb = recb + 6;      // superclump ends
+    const int* cum = recb + 6 + ks;  // cum[r][t] at r * ks + t
     if (P.trace.d_sc_ends && ks <= P.trace.sc_stride)
       for (int j = lane; j <= k; j += 32) P.trace.d_sc_ends[trace_task * P.trace.sc_stride + j] = rec[6 + j];
     __syncwarp();
 
     if (k >= 2) {
-      // lanes as (level, phase): LP level groups of P phases
-      const int nlev = lmax - 1;
-      const int LP = nlev <= 1 ? 1 : nlev <= 2 ? 2 : nlev <= 4 ? 4 : 8;
-      const int Pph = 32 / LP;
-      const int li = lane / Pph;
-      const int ph = lane - li * Pph;
-      const int lv = 2 + li;  // this lane's level
-      // entropy columns double-buffered: column t+1 is formed before the
-      // levels of t are reduced, so its loads overlap that work
-      real* const Ec0 = Ecol;
-      real* const Ec1 = Ecol + S.LE;
-      if (lane == 0) Ec1[0] = E_small<real>(Lt, scb, cum, ks, yhat, 0, 1);
-      __syncwarp();
-      for (int t = 1; t <= k; ++t) {
-        const real* Et = (t & 1) ? Ec1 : Ec0;
-        if (t < k) {
-          real* En = (t & 1) ? Ec0 : Ec1;
-          for (int s = lane; s <= t; s += 32) En[s] = E_small<real>(Lt, scb, cum, ks, yhat, s, t + 1);
+      // ---- the entropy triangle: entry f = tri_row(s,k) + t - s - 1 in
+      // lane f mod 32, two entries (f, f + 32) at a time, (s, t) advancing
+      // along the rows
+      {
+        const int npairs = k * (k + 1) / 2;
+        int s = 0, pos = lane;  // pos = t - s - 1 within row s (k - s entries)
+        auto advance = [&](int d) {
+          pos += d;
+          while (s < k && pos >= k - s) {
+            pos -= k - s;
+            ++s;
+          }
+        };
+        advance(0);
+        for (int f = lane; f < npairs; f += 64) {
+          const int s1 = s, t1 = s + 1 + pos;
+          advance(32);
+          const bool two = f + 32 < npairs;
+          const int s2 = two ? s : s1, t2 = two ? s + 1 + pos : t1;
+          real e1, e2;
+          E_small2<real>(Lt, scb, cum, ks, yhat, s1, t1, s2, t2, e1, e2);
+          Et[f] = e1;
+          if (two) Et[f + 32] = e2;
+          advance(32);
         }
-        const int lt = min(t, lmax);
-        real best = NINF;
-        int arg = 0x7fffffff;
-        if (lv <= lt) {
-          for (int s = lv - 1 + ph; s < t; s += Pph) {
-            const real v = W[s * LW + (lv - 1)] - Et[s];
-            if (v > best) {
+      }
+      __syncwarp();
+      // ---- W(t,1) = -E(0,t)
+      for (int t = 1 + lane; t <= k; t += 32) {
+        W[t * LW + 1] = -Et[t - 1];
+        A[t * LW + 1] = 0;
+      }
+      __syncwarp();
+      // ---- levels 2 .. lmax-1 at every t >= l: lanes over t, s upwards
+      for (int l = 2; l < lmax; ++l) {
+        for (int t0 = l; t0 <= k; t0 += 32) {
+          const int t = t0 + lane;
+          const int tt = min(t, k);
+          real best = NINF;
+          int arg = l - 1;
+          const int s_hi = min(t0 + 31, k);  // the warp's bound: s < the largest t
+          for (int s = l - 1; s < s_hi; ++s) {
+            const real v = W[s * LW + (l - 1)] - Et[tri_row(s, k) + tt - s - 1];
+            if (s < t && v > best) {
               best = v;
               arg = s;
             }
           }
+          if (t <= k) {
+            const real wt = W[t * LW + (l - 1)];  // s = t, the empty column
+            if (wt > best) {
+              best = wt;
+              arg = t;
+            }
+            W[t * LW + l] = best;
+            A[t * LW + l] = (int16_t)arg;
+          }
         }
-        for (int d = Pph >> 1; d > 0; d >>= 1) {
+        __syncwarp();
+      }
+      // ---- the last level at t = k only: lanes over s, the first maximum
+      {
+        const int l = lmax;
+        real best = NINF;
+        int arg = 0x7fffffff;
+        for (int s = l - 1 + lane; s <= k; s += 32) {
+          const real wv = W[s * LW + (l - 1)];
+          const real v = s < k ? wv - Et[tri_row(s, k) + k - s - 1] : wv;
+          if (v > best) {
+            best = v;
+            arg = s;
+          }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
           const real ob = __shfl_xor_sync(0xffffffffu, best, d);
           const int oa = __shfl_xor_sync(0xffffffffu, arg, d);
           if (ob > best || (ob == best && oa < arg)) {
@@ -150,60 +235,49 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
             arg = oa;
           }
         }
-        if (ph == 0 && lv <= lt) {
-          Vb[lv] = best;
-          Va[lv] = arg;
-        }
-        __syncwarp();
         if (lane == 0) {
-          real cur = -Et[0];  // W(t,1)
-          W[t * LW + 1] = cur;
-          A[t * LW + 1] = 0;
-          for (int l = 2; l <= lt; ++l) {
-            const real v = Vb[l];
-            int a;
-            if (cur > v) {  // s = t: W(t,l-1) - E(t,t) is the larger
-              a = t;
-            } else {
-              cur = v;
-              a = Va[l];
-            }
-            W[t * LW + l] = cur;
-            A[t * LW + l] = (int16_t)a;
-          }
+          W[k * LW + l] = best;
+          A[k * LW + l] = (int16_t)arg;
         }
-        __syncwarp();
       }
-      // chosen partitions: lane l-2 follows A back from (k, l)
-      const int l = 2 + lane;
-      if (l <= lmax) {
-        int* cut = cuts + (l - 2) * LW;
-        int tcur = k;
-        for (int v = l; v >= 2; --v) {
-          const int s = A[tcur * LW + v];
-          cut[v - 2] = s;
-          tcur = s;
-        }
-        double I;
-        if constexpr (fp32) {
-          // re-score in double, in the DP's own order
-          int prev = 0;
-          double w = 0.0;
-          for (int c = 0; c < l; ++c) {
-            const int bnd = c == l - 1 ? k : cut[c];
-            double e = P.L64[scb[bnd] - scb[prev]];
-            for (int r = 0; r < yhat; ++r) e -= P.L64[cum[r * ks + bnd] - cum[r * ks + prev]];
-            w = c == 0 ? -e : w - e;
-            prev = bnd;
+      __syncwarp();
+      // ---- chosen partitions: lane l-2 follows A back from (k, l)
+      {
+        const int l = 2 + lane;
+        if (l <= lmax) {
+          int* cut = cuts + (l - 2) * LW;
+          int tcur = k;
+          for (int v = l; v >= 2; --v) {
+            const int s = A[tcur * LW + v];
+            cut[v - 2] = s;
+            tcur = s;
           }
-          I = HQ + w / (double)n;
-        } else {
-          I = HQ + (double)W[k * LW + l] / (double)n;
+          if constexpr (!fp32) Iw[l] = HQ + (double)W[k * LW + l] / (double)n;
+          if (P.trace.d_cuts) {
+            int32_t* dst = P.trace.d_cuts + trace_task * P.trace.cut_stride + (l - 2) * (l - 1) / 2;
+            for (int c = 0; c < l - 1; ++c) dst[c] = cut[c];
+          }
         }
-        Iw[l] = I;
-        if (P.trace.d_cuts) {
-          int32_t* dst = P.trace.d_cuts + trace_task * P.trace.cut_stride + (l - 2) * (l - 1) / 2;
-          for (int c = 0; c < l - 1; ++c) dst[c] = cut[c];
+      }
+      __syncwarp();
+      if constexpr (fp32) {
+        // re-score each chosen partition in double: the terms (column c,
+        // row r) over the lanes, then a warp sum
+        for (int l = 2; l <= lmax; ++l) {
+          const int* cut = cuts + (l - 2) * LW;
+          const int nt = l * (yhat + 1);
+          double part = 0.0;
+          for (int i = lane; i < nt; i += 32) {
+            const int c = i / (yhat + 1), r = i - c * (yhat + 1);
+            const int a = c == 0 ? 0 : cut[c - 1];
+            const int b = c == l - 1 ? k : cut[c];
+            // -E(a,b) = -L(c_b - c_a) + sum_r L(cum[r][b] - cum[r][a])
+            part += r == 0 ? -P.L64[scb[b] - scb[a]]
+                           : P.L64[cum[(r - 1) * ks + b] - cum[(r - 1) * ks + a]];
+          }
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+          if (lane == 0) Iw[l] = HQ + part / (double)n;
         }
       }
       __syncwarp();
@@ -222,10 +296,11 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
     }
     if (lane == 0 && yhat < 2) atomicOr(&P.pp.flags[pl], 1 << GMINE_E_CONSTANT);
     if (lane == 0 && k >= 2 && lmax >= 2) {
-      const long long L = lmax, K = k;
-      long long cand = (L + 1) * L * (L - 1) / 6;
-      const long long tsum = (K * (K + 1) - L * (L + 1)) / 2;
-      cand += (L - 1) * tsum - (K - L) * (L - 1) * L / 2;
+      // the W candidates formed: the levels below the last at every t >= l,
+      // the last at t = k
+      long long cand = 0;
+      for (int l = 2; l < lmax; ++l) cand += (long long)(k - l + 1) * (k - l + 2) / 2;
+      cand += k - lmax + 2;
       cand_sum += cand;
     }
     if (lane == 0) ++task_sum;

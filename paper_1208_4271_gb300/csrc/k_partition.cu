@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
     int32_t* rec0 = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient;
     if (n < 4 || B < 4) {
       for (int y = 2 + (int)threadIdx.x; y <= P.B_full / 2; y += blockDim.x) {
-        int32_t* rec = rec0 + rec_offset(P.B_full, P.n_full, P.c, y);
+        int32_t* rec = rec0 + P.rec_off[y];
         rec[0] = 0;
         rec[1] = 0;
         rec[2] = 0;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
     __syncthreads();
 
     for (int y = 2 + wib; y <= P.B_full / 2; y += NWp) {
-      int32_t* rec = rec0 + rec_offset(P.B_full, P.n_full, P.c, y);
+      int32_t* rec = rec0 + P.rec_off[y];
       if (y > B / 2) {  // fewer samples than the batch's n: no such task
         if (lane == 0) {
           rec[0] = 0;

@@ -8,7 +8,8 @@ namespace gm {
 
 // L(m) = m ln m (L(0) = 0), its float rounding, and ln m, for m = 0..n
 // (Appendix items 9-10: entropies in nats from cell counts).
-__global__ void k_tables(int n, double* L64, float* L32, double* lnt) {
+__global__ void k_tables(int n, double* L64, float* L32, double* lnt, int B, double c,
+                         int64_t* rec_off) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= n;
        m += gridDim.x * blockDim.x) {
     const double lm = m > 0 ? log((double)m) : 0.0;
@@ -17,6 +18,9 @@ __global__ void k_tables(int n, double* L64, float* L32, double* lnt) {
     L32[m] = (float)L;
     lnt[m] = lm;
   }
+  // first int of the records of row count y within a (pair, orientation)
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y <= B / 2 + 1; y += gridDim.x * blockDim.x)
+    rec_off[y] = y >= 2 ? rec_offset(B, n, c, y) : 0;
 }
 
 // Non-finite samples per variable (one warp per variable, coalesced rows).

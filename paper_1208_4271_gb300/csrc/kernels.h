@@ -8,7 +8,8 @@
 
 namespace gm {
 
-__global__ void k_tables(int n, double* L64, float* L32, double* lnt);
+__global__ void k_tables(int n, double* L64, float* L32, double* lnt, int B, double c,
+                         int64_t* rec_off);
 __global__ void k_nonfinite(const double* vars, int64_t p, int n, int32_t* nf);
 __global__ void k_pair_prep(const int32_t* pairs, int64_t pair0, int64_t chunk,
                             int64_t p, int n, const int32_t* nf,
@@ -48,6 +49,9 @@ GM_DP_DECLARE(dp_f64_smem)
 GM_DP_DECLARE(dp_f64_global)
 #undef GM_DP_DECLARE
 
+cudaError_t dp_two_configure(bool fp32, int smem, int threads, int* blocks_per_sm);
+cudaError_t dp_two_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
+                          const DPParams& P, int off_rec, int rec_bytes);
 cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_sm, bool set_attr);
 cudaError_t dp_mid_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
                           const DPParams& P, const MidPlan& S);
