@@ -114,6 +114,7 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
   S.off_X = add(xbytes);
   S.off_Eb = add((int64_t)32 * 33 * rs);
+  S.off_rbuf = add((int64_t)2 * 32 * rs);
   S.off_Rtop = add((int64_t)(tb.kmax + 1) * rs);
   S.off_sd = add(4LL * std::max(tb.sd_max, 4));
   const int reserve = 1024;

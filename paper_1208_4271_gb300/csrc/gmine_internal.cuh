@@ -268,7 +268,7 @@ struct MidPlan {
 
 // Shared-memory layout of the DP kernel (byte offsets).
 struct DPPlan {
-  int off_R, off_Rtop, off_X, off_Eb, off_L, off_sd;
+  int off_R, off_Rtop, off_X, off_Eb, off_rbuf, off_L, off_sd;
   int off_I_rel, off_lst_rel;  // traceback scratch inside the X region
   int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4
   int LX;     // row stride of the X buffers: levels 1..lmax, odd (the lanes'

@@ -28,8 +28,6 @@
 // -0.0, negative or -inf, so a larger value has smaller bits).  Levels
 // beyond a task's last level hold -inf, so no candidate needs a guard.
 #pragma once
-#include <type_traits>
-
 #include "gmine_internal.cuh"
 #include "kernels.h"
 
@@ -244,33 +242,58 @@ __host__ __device__ __forceinline__ int level_group(int nlev) {
   return 40;
 }
 
-// The candidates of block b with s inside the block, one t after another,
-// with the block's earlier rows kept in registers (at most 32 levels, level
-// 2 + lane in lane `lane`): right after step i, the lane of level l receives
-// R(t0+i, l-1) from the lane of level l-1 by one shuffle, so step j reads
-// registers and the broadcast E column only.  The 32 steps are unrolled so
-// that every register index is static.
+// The candidates of block b with s inside the block, level after level:
+// lane j owns t0+j and keeps the column E(t0+i, t0+j), i < j, in registers
+// (+inf for i >= j, so those candidates are -inf).  At level l the 32
+// values R(t0+i, l-1) of the previous level sit in a 32-entry buffer and
+// reach every lane as eight 16-byte broadcast loads (two buffers, one per
+// level parity); R(t0+j, l) is the maximum of the partial X(t0+j, l) from
+// the earlier blocks and the in-block candidates.  The chain is the levels,
+// each about sixty instructions, for any number of levels.
 template <typename real>
-__device__ __forceinline__ void phase_b_regs(real* __restrict__ Rt, real* __restrict__ Rtop, int LS,
-                                             int LX, int lmax, int t0, int k,
-                                             const typename Bits<real>::U* __restrict__ Xcur,
-                                             bool has_x, const real* __restrict__ Eb, int lane) {
+__device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __restrict__ Rtop, int LS,
+                                              int LX, int lmax, int t0, int k,
+                                              const typename Bits<real>::U* __restrict__ Xcur,
+                                              bool has_x, const real* __restrict__ Eb,
+                                              real* __restrict__ rbuf, int lane) {
   using BT = Bits<real>;
-  const int l = 2 + lane;
-  const bool live = l <= lmax;
-  real prev[32];
+  constexpr int VW = 16 / sizeof(real);
+  const int t = t0 + lane;
+  const bool tv = t <= k;
+  real pinf;
+  if constexpr (sizeof(real) == 4) pinf = __int_as_float(0x7f800000);
+  else pinf = __longlong_as_double(0x7ff0000000000000ll);
+  real ec[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (t0 + j > k) break;
-    const int tj = t0 + j;
-    real v = (has_x && live) ? BT::from(Xcur[j * LX + (l - 1)]) : BT::ninf();
+  for (int i = 0; i < 32; ++i) ec[i] = (tv && i < lane) ? Eb[i * 33 + lane] : pinf;
+  real rcur = tv ? Rt[t * LS] : BT::ninf();  // level 1
+  const typename Bits<real>::U* xr = Xcur + lane * LX;
+  int par = 0;
+#pragma unroll 1
+  for (int l = 2; l <= lmax; ++l) {
+    real* rb = rbuf + par * 32;
+    rb[lane] = rcur;
+    __syncwarp();
+    real m0 = has_x ? BT::from(xr[l - 1]) : BT::ninf();
+    real m1 = BT::ninf();
 #pragma unroll
-    for (int i = 0; i < j; ++i) v = BT::max(v, prev[i] - Eb[i * 33 + j]);
-    if (live) {
-      if (l == lmax) Rtop[tj] = v; else Rt[tj * LS + (l - 1)] = v;
+    for (int q = 0; q < 32 / VW; ++q) {
+      if constexpr (sizeof(real) == 4) {
+        const float4 r = reinterpret_cast<const float4*>(rb)[q];
+        m0 = fmax3(m0, r.x - ec[4 * q + 0], r.y - ec[4 * q + 1]);
+        m1 = fmax3(m1, r.z - ec[4 * q + 2], r.w - ec[4 * q + 3]);
+      } else {
+        const double2 r = reinterpret_cast<const double2*>(rb)[q];
+        m0 = BT::max(m0, r.x - ec[2 * q + 0]);
+        m1 = BT::max(m1, r.y - ec[2 * q + 1]);
+      }
     }
-    const real below = __shfl_sync(0xffffffffu, v, (lane + 31) & 31);
-    prev[j] = lane == 0 ? Rt[tj * LS] : below;
+    const real v = BT::max(m0, m1);
+    if (tv) {
+      if (l == lmax) Rtop[t] = v; else Rt[t * LS + (l - 1)] = v;
+    }
+    rcur = tv ? v : BT::ninf();
+    par ^= 1;
   }
 }
 
@@ -297,6 +320,7 @@ k_dp(DPParams P, DPPlan S) {
   real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // [kmax+1]
   U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // [32][33]
+  real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   int* sd = reinterpret_cast<int*>(sm + S.off_sd);        // [kmax+1][SW]
   // after the DP the X buffers hold the traceback scratch
   int* cuts = reinterpret_cast<int*>(sm + S.off_X);                       // [4 NW][xmax]
@@ -386,54 +410,8 @@ k_dp(DPParams P, DPPlan S) {
         const bool tnv = next && tn <= k;
         const int ttn = tnv ? tn : k;
         for (int step = 0; step < 2; ++step) {
-          if (step == 0 && warp == 0) {
-            // ---- block b, s inside the block: one t after another
-            if (std::is_same<real, float>::value && LEV <= 24 && lmax - 1 <= 32) {
-              phase_b_regs<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, Eb, lane);
-            } else {
-              // many levels: lanes over levels, two per lane per pass
-              for (int j = 0; j < 32 && t0 + j <= k; ++j) {
-                const int tj = t0 + j;
-                for (int lb = 2; lb <= lmax; lb += 64) {
-                  const int la = lb + lane, lc2 = lb + 32 + lane;
-                  const bool va = la <= lmax, vb = lc2 <= lmax;
-                  real a0 = NINF, a1 = NINF, b0 = NINF, b1 = NINF;
-                  if (b > 0) {
-                    if (va) a0 = BT::from(Xcur[j * LX + (la - 1)]);
-                    if (vb) b0 = BT::from(Xcur[j * LX + (lc2 - 1)]);
-                  }
-                  const real* Ra = Rt + t0 * LS + (la - 2);
-                  const real* Rb = Rt + t0 * LS + (lc2 - 2);
-                  int i = 0;
-                  for (; i + 1 < j; i += 2) {
-                    const real e0 = Eb[i * 33 + j], e1 = Eb[(i + 1) * 33 + j];
-                    if (va) {
-                      a0 = BT::max(a0, Ra[i * LS] - e0);
-                      a1 = BT::max(a1, Ra[(i + 1) * LS] - e1);
-                    }
-                    if (vb) {
-                      b0 = BT::max(b0, Rb[i * LS] - e0);
-                      b1 = BT::max(b1, Rb[(i + 1) * LS] - e1);
-                    }
-                  }
-                  if (i < j) {
-                    const real e0 = Eb[i * 33 + j];
-                    if (va) a0 = BT::max(a0, Ra[i * LS] - e0);
-                    if (vb) b0 = BT::max(b0, Rb[i * LS] - e0);
-                  }
-                  if (va) {
-                    const real v = BT::max(a0, a1);
-                    if (la == lmax) Rtop[tj] = v; else Rt[tj * LS + (la - 1)] = v;
-                  }
-                  if (vb) {
-                    const real v = BT::max(b0, b1);
-                    if (lc2 == lmax) Rtop[tj] = v; else Rt[tj * LS + (lc2 - 1)] = v;
-                  }
-                }
-                __syncwarp();
-              }
-            }
-          }
+          if (step == 0 && warp == 0)  // ---- block b, s inside the block
+            phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, Eb, rbuf, lane);
           // step 0: A1 of block b+1, s in [1, t0 - 1], shared work counter
           // (warp 0 joins once block b is solved);
           // step 1: A2 of block b+1, s in block b, static split

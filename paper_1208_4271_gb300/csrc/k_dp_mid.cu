@@ -2,17 +2,19 @@
 // precomputations of Appendix item 10), one CTA per task, level after level,
 // for tasks whose whole entropy triangle fits in shared memory.
 //
-// The recursion is the one of k_dp.cu without empty columns,
+// The recursion is the one of k_dp.cuh without empty columns,
 //   R(t,1) = -E(0,t),  R(t,l) = max_{s in [l-1, t-1]} R(s,l-1) - E(s,t),
 // whose prefix maximum over levels is the method's W(t,l) exactly.  Within a
 // level every t is independent, so the only sequential chain is the levels
 // (x - 1 of them) instead of the superclumps (k of them).  E(s,t) for all
-// s < t (Appendix item 10b: the entropy matrix) is formed once with every
-// thread busy; each level then runs over tiles of 32 t (lanes) by CH s
-// taken from a shared counter: the R row entry is a warp-wide broadcast,
-// E(s, t..t+31) 32 consecutive words, and the tile's maxima join the level
-// row through atomicMin on the value bits (every value is -0.0, negative or
-// -inf, so a larger value has smaller bits).
+// s < t (Appendix item 10b: the entropy matrix) is formed once, warps over
+// rows s and lanes over t.  Each level below the last then runs over tiles
+// of 32 t (lanes) by 32 s dealt round-robin to the warps: the R row entry is
+// a warp-wide broadcast, E(s, t..t+31) 32 consecutive words, and the tile's
+// maxima join the level row through atomicMin on the value bits (every
+// value is -0.0, negative or -inf, so a larger value has smaller bits).  The
+// last level is needed at t = k only (W(k,l) and the tracebacks never read
+// it elsewhere): one CTA-wide maximum.
 #include "gmine_internal.cuh"
 #include "kernels.h"
 
@@ -60,6 +62,41 @@ __device__ __forceinline__ real entropy_mid(const real* __restrict__ Lt, const i
   return e;
 }
 
+// E(s,t1) and E(s,t2) with their loads interleaved (two independent chains,
+// each in increasing r)
+template <typename real>
+__device__ __forceinline__ void entropy_mid2(const real* __restrict__ Lt, const int* __restrict__ scb,
+                                             const int* __restrict__ cum, int ks, int yhat, int s,
+                                             int t1, int t2, real& e1, real& e2) {
+  real a = Lt[scb[t1] - scb[s]];
+  real b = Lt[scb[t2] - scb[s]];
+  const int* __restrict__ cs = cum + s;
+  const int* __restrict__ c1 = cum + t1;
+  const int* __restrict__ c2 = cum + t2;
+  int r = 0;
+  for (; r + 4 <= yhat; r += 4) {
+    real la[4], lb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int v = cs[(r + q) * ks];
+      la[q] = Lt[c1[(r + q) * ks] - v];
+      lb[q] = Lt[c2[(r + q) * ks] - v];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a -= la[q];
+      b -= lb[q];
+    }
+  }
+  for (; r < yhat; ++r) {
+    const int v = cs[r * ks];
+    a -= Lt[c1[r * ks] - v];
+    b -= Lt[c2[r * ks] - v];
+  }
+  e1 = a;
+  e2 = b;
+}
+
 // offset of E(s, .) in the packed triangle: row s holds t = s+1 .. k
 __device__ __forceinline__ int tri_row(int s, int k) { return s * k - (s * (s - 1)) / 2; }
 
@@ -69,14 +106,12 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
   using U = typename BT::U;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_task;
-  __shared__ int s_next;
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const int NW = T >> 5;
   constexpr bool fp32 = sizeof(real) == 4;
-  constexpr int CH = 16;  // s per tile
 
   real* Et = reinterpret_cast<real*>(sm + S.off_E);      // packed triangle
   real* Rl = reinterpret_cast<real*>(sm + S.off_R);      // [lmax+1][KS]: R(t,l) at l*KS+t
@@ -91,7 +126,6 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
     if constexpr (fp32) Lsrc = P.L32; else Lsrc = P.L64;
     for (int m = tid; m <= P.n_full; m += T) Lt[m] = Lsrc[m];
   }
-  if (tid == 0) s_next = 0;
   const real NINF = BT::ninf();
   const int64_t C = P.chunk_pairs;
 
@@ -131,56 +165,66 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
     __syncthreads();
 
     if (k >= 2) {
-      // the entropy triangle, every thread busy
-      const int npairs = k * (k + 1) / 2;
-      for (int f = tid; f < npairs; f += T) {
-        // invert f = tri_row(s, k) + (t - s - 1): a float estimate, then exact steps
-        const float kk = 2.0f * (float)k + 1.0f;
-        int s = (int)((kk - sqrtf(fmaxf(kk * kk - 8.0f * (float)f, 0.0f))) * 0.5f);
-        if (s < 0) s = 0;
-        if (s > k - 1) s = k - 1;
-        while (s > 0 && tri_row(s, k) > f) --s;
-        while (s < k - 1 && tri_row(s + 1, k) <= f) ++s;
-        const int t = f - tri_row(s, k) + s + 1;
-        Et[f] = entropy_mid<real>(Lt, scb, cum, ks, yhat, s, t);
+      // ---- the entropy triangle: warps over rows s, lanes over t = s+1..k,
+      // two entries per lane in flight
+      for (int s = warp; s < k; s += NW) {
+        real* row = Et + tri_row(s, k) - s - 1;  // row[t] = E(s,t)
+        for (int t = s + 1 + lane; t <= k; t += 64) {
+          const bool two = t + 32 <= k;
+          real e1, e2;
+          entropy_mid2<real>(Lt, scb, cum, ks, yhat, s, t, two ? t + 32 : t, e1, e2);
+          row[t] = e1;
+          if (two) row[t + 32] = e2;
+        }
       }
       // level 1; every other level starts at -inf
       for (int i = tid; i < (lmax + 1) * KS; i += T) Rl[i] = NINF;
       __syncthreads();
       for (int t = 1 + tid; t <= k; t += T) Rl[KS + t] = -Et[tri_row(0, k) + t - 1];
       __syncthreads();
-      // levels
-      for (int l = 2; l <= lmax; ++l) {
+      // ---- levels 2 .. lmax-1 at every t >= l: tiles of 32 t (lanes) by
+      // 32 s, the non-empty ones (some s < t) dealt round-robin to the
+      // warps; a tile's maxima join the level row through atomicMin on the
+      // value bits (distinct t per lane: no bank conflicts)
+      for (int l = 2; l < lmax; ++l) {
         const real* Rp = Rl + (l - 1) * KS;
         U* Rc = reinterpret_cast<U*>(Rl + l * KS);
-        // tiles: t-blocks [tb, tb+32) with tb = l + 32 i, s-chunks [sb, sb+CH)
-        // with sb = l-1 + CH j, s < t, taken from the counter in order
-        const int nt = (k - l + 1 + 31) / 32;
-        const int ns = (k - l + 1 + CH - 1) / CH;  // s runs over [l-1, k-1]
-        for (;;) {
-          int g = 0;
-          if (lane == 0) g = atomicAdd(&s_next, 1);
-          g = __shfl_sync(0xffffffffu, g, 0);
-          if (g >= nt * ns) break;
-          const int it = g / ns, js = g - it * ns;
-          const int tb = l + 32 * it;
-          const int sb = l - 1 + CH * js;
-          if (sb >= tb + 31) continue;  // no s < t in this tile
-          const int t = tb + lane;
-          const bool tv = t <= k;
-          const int s_end = min(sb + CH, k);  // exclusive
+        const int nt = (k - l + 1 + 31) / 32;  // t-chunks [l + 32 i, l + 32 i + 31]
+        // t-chunk i has s-pieces j = 0..i (s in [l-1 + 32 j, l + 32 j + 30]):
+        // tile g = i (i + 1) / 2 + j
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int g = warp; g < ntiles; g += NW) {
+          int i = (int)((sqrtf(8.0f * (float)g + 1.0f) - 1.0f) * 0.5f);
+          while (i * (i + 1) / 2 > g) --i;
+          while ((i + 1) * (i + 2) / 2 <= g) ++i;
+          const int j = g - i * (i + 1) / 2;
+          const int t = l + 32 * i + lane;
+          const int tt = min(t, k);
+          const int sb = l - 1 + 32 * j;
+          const int se = min(sb + 32, min(l + 32 * i + 31, k));  // s < the chunk's largest t
           real acc = NINF;
-          if (tv) {
-            const int s_hi = min(s_end, t);  // s < t
+          int base = tri_row(sb, k) + tt - sb - 1;  // E(sb, tt); row s+1 starts k-s-1 later
 #pragma unroll 4
-            for (int s = sb; s < s_hi; ++s) acc = BT::max(acc, Rp[s] - Et[tri_row(s, k) + t - s - 1]);
+          for (int s = sb; s < se; ++s) {
+            const real v = Rp[s] - Et[base];
+            if (s < t) acc = BT::max(acc, v);
+            base += k - s - 1;
           }
-          if (tv && acc != NINF) atomicMin(&Rc[t], BT::of(acc));
+          if (t <= k && acc != NINF) atomicMin(&Rc[t], BT::of(acc));
         }
         __syncthreads();
-        if (tid == 0) s_next = 0;
-        __syncthreads();
       }
+      // ---- the last level at t = k only: R(k, lmax) over s in [lmax-1, k-1]
+      {
+        const int l = lmax;
+        const real* Rp = Rl + (l - 1) * KS;
+        real acc = NINF;
+        for (int s = l - 1 + tid; s < k; s += T) acc = BT::max(acc, Rp[s] - Et[tri_row(s, k) + k - s - 1]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc = BT::max(acc, __shfl_xor_sync(0xffffffffu, acc, d));
+        if (lane == 0 && acc != NINF) atomicMin(reinterpret_cast<U*>(Rl + l * KS) + k, BT::of(acc));
+      }
+      __syncthreads();
     }
 
     // ---- I(l) for l = 2..x
