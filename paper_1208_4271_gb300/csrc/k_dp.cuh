@@ -488,12 +488,20 @@ k_dp(DPParams P, DPPlan S) {
           int lv = lstar, tcur = k, s0 = k - 1;
           bool going = act && lv >= 2;
           real target = going ? Rget(k, lv) : NINF;
+          // row tcur in registers while it is the target's t (short rows)
+          const bool reg = yhat <= 7;
+          int td[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) td[c] = (reg && c < SW) ? sd[tcur * SW + c] : 0;
           while (__any_sync(0xffffffffu, going)) {
             const int s = s0 - sub;
             bool hit = false;
             if (going && s >= lv - 1) {
+              // the filter value and E(s, tcur) side by side
               const real r = Rt[s * LS + (lv - 2)];
-              if (r >= target) hit = r - entropy_term<real>(Lt, sd, SW, yhat, s, tcur) == target;
+              const real e = reg ? entropy_reg<real>(Lt, sd, SW, yhat, td, s)
+                                 : entropy_term<real>(Lt, sd, SW, yhat, s, tcur);
+              hit = r >= target && r - e == target;
             }
             const unsigned m = (__ballot_sync(0xffffffffu, hit) >> (8 * grp)) & 0xffu;
             if (going) {
@@ -505,7 +513,13 @@ k_dp(DPParams P, DPPlan S) {
                 tcur = found;
                 --lv;
                 s0 = tcur - 1;
-                if (lv >= 2) target = Rget(tcur, lv); else going = false;
+                if (lv >= 2) {
+                  target = Rget(tcur, lv);
+#pragma unroll
+                  for (int c = 0; c < 8; ++c) td[c] = (reg && c < SW) ? sd[tcur * SW + c] : 0;
+                } else {
+                  going = false;
+                }
               } else {
                 s0 -= 8;
               }
