@@ -25,9 +25,10 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
 __global__ void __launch_bounds__(128) k_partition(PartParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_job;
+  __shared__ int s_y;                    // next row count of the current (pair, o)
+  __shared__ unsigned s_magic[kMagicN];  // exact division by the row counts left
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int NWp = blockDim.x >> 5;
   uint16_t* pi = reinterpret_cast<uint16_t*>(sm + P.off_pi);   // [n] U position -> V position
   uint16_t* gU = reinterpret_cast<uint16_t*>(sm + P.off_gU);   // [n] U position -> tie group
   unsigned char* my = sm + P.off_warps + (int64_t)wib * P.warp_smem;
@@ -43,8 +44,12 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
   const int64_t C = P.chunk_pairs;
   const int R = P.eq.R;
   const int64_t st = P.rk.stride;
+  for (int d = threadIdx.x; d < kMagicN; d += blockDim.x) s_magic[d] = d >= 2 ? magic_of(d) : 0u;
   for (;;) {
-    if (threadIdx.x == 0) s_job = (long long)atomicAdd(P.queue, 1ull);
+    if (threadIdx.x == 0) {
+      s_job = (long long)atomicAdd(P.queue, 1ull);
+      s_y = 2;
+    }
     __syncthreads();
     const int64_t job = s_job;
     __syncthreads();
@@ -75,7 +80,13 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
     }
     __syncthreads();
 
-    for (int y = 2 + wib; y <= P.B_full / 2; y += NWp) {
+    // row counts taken in increasing order (the long superclump chains of
+    // the small y first) by whichever warp is free
+    for (;;) {
+      int yy = 0;
+      if (lane == 0) yy = atomicAdd(&s_y, 1);
+      const int y = __shfl_sync(0xffffffffu, yy, 0);
+      if (y > P.B_full / 2) break;
       int32_t* rec = rec0 + P.rec_off[y];
       if (y > B / 2) {  // fewer samples than the batch's n: no such task
         if (lane == 0) {
@@ -88,7 +99,9 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       const int yhat = P.eq.yhat[(int64_t)sV * R + (y - 2)];
       const int32_t* gb = P.eq.bounds + ((int64_t)sV * R + (y - 2)) * P.eq.bstride;
       for (int j = lane; j <= yhat; j += 32) eb[j] = gb[j];
-      for (int w = lane; w < (GU + 31) / 32; w += 32) mixed[w] = 0u;
+      const bool ties = GU < n;  // else every tie run is one point: none is mixed
+      if (ties)
+        for (int w = lane; w < (GU + 31) / 32; w += 32) mixed[w] = 0u;
       __syncwarp();
       // rows of the V-sorted positions, then of the U-sorted positions
       for (int j = 0; j < yhat; ++j)
@@ -98,10 +111,11 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       __syncwarp();
       // x-tie runs whose rows are mixed get one fresh label (Algorithm
       // GetClumpsPartition, first pass; one label per run)
-      for (int m = 1 + lane; m < n; m += 32) {
-        const int g = gU[m];
-        if (g == gU[m - 1] && q[m] != q[m - 1]) atomicOr(&mixed[g >> 5], 1u << (g & 31));
-      }
+      if (ties)
+        for (int m = 1 + lane; m < n; m += 32) {
+          const int g = gU[m];
+          if (g == gU[m - 1] && q[m] != q[m - 1]) atomicOr(&mixed[g >> 5], 1u << (g & 31));
+        }
       __syncwarp();
       // a clump starts where the label changes (second pass): ballot per 32
       int nc = 0;
@@ -112,8 +126,12 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
           if (m == 0) {
             f = true;
           } else {
-            const int g = gU[m], gp = gU[m - 1];
-            f = g != gp && (bit_of(mixed, g) || bit_of(mixed, gp) || q[m] != q[m - 1]);
+            if (ties) {
+              const int g = gU[m], gp = gU[m - 1];
+              f = g != gp && (bit_of(mixed, g) || bit_of(mixed, gp) || q[m] != q[m - 1]);
+            } else {
+              f = q[m] != q[m - 1];
+            }
           }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, f);
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       const bool superclump = nc > khat;
       if (superclump) {
         int kk = 0;
-        if (lane == 0) kk = equipartition_bounds_u16(cstart, cgrp, nc, n, khat, scb);
+        if (lane == 0) kk = equipartition_bounds_u16(cstart, cgrp, nc, n, khat, scb, s_magic);
         k = __shfl_sync(0xffffffffu, kk, 0);
       } else {
         for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
