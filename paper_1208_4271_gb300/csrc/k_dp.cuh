@@ -239,6 +239,7 @@ __host__ __device__ __forceinline__ int level_group(int nlev) {
   if (nlev <= 20) return 20;
   if (nlev <= 24) return 24;
   if (nlev <= 32) return 32;
+  if (nlev <= 36) return 36;
   return 40;
 }
 
@@ -526,14 +527,21 @@ k_dp(DPParams P, DPPlan S) {
             }
           }
           __syncwarp();
-          // -E(0,s_1) - E(s_1,s_2) - ... - E(s_{l*-1},k) in double
+          // -E(0,s_1) - E(s_1,s_2) - ... - E(s_{l*-1},k) in double: the
+          // terms (column c, row r) spread over the group's lanes, all loads
+          // independent
           double part = 0.0;
-          if (act)
-            for (int c = sub; c < lstar; c += 8) {
+          if (act) {
+            const int nt = lstar * (yhat + 1);
+            for (int i = sub; i < nt; i += 8) {
+              const int c = i / (yhat + 1), r = i - c * (yhat + 1);
               const int a = c == 0 ? 0 : gcut[c - 1];
               const int bnd = c == lstar - 1 ? k : gcut[c];
-              part -= entropy_term<double>(P.L64, sd, SW, yhat, a, bnd);
+              // r = 0: -L(c_b - c_a); r >= 1: + L(cum[r-1][b] - cum[r-1][a])
+              const double L = P.L64[sd[bnd * SW + r] - sd[a * SW + r]];
+              part += r == 0 ? -L : L;
             }
+          }
           part += __shfl_xor_sync(0xffffffffu, part, 4);
           part += __shfl_xor_sync(0xffffffffu, part, 2);
           part += __shfl_xor_sync(0xffffffffu, part, 1);
