@@ -326,7 +326,7 @@ def main():
             "plain_fp64": fp64,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcand/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_mid, k_dp_small)",
+                         "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_mid, k_dp_small, k_dp_two)",
                          "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr per DP step"
                                        % (sms, fmax),
                          "dp_candidates_per_step": cand // max(args.steps, 1),
