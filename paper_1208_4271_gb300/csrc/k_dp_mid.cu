@@ -39,6 +39,13 @@ struct MBits<double> {
   __device__ static double max(double a, double b) { return fmax(a, b); }
 };
 
+__device__ __forceinline__ float mid_max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ double mid_max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
 // E(s,t) = L(c_t - c_s) - sum_r L(cum[r][t] - cum[r][s]), increasing r
 template <typename real>
 __device__ __forceinline__ real entropy_mid(const real* __restrict__ Lt, const int* __restrict__ scb,
@@ -204,11 +211,23 @@ __global__ void __launch_bounds__(256) k_dp_mid(DPParams P, MidPlan S) {
           const int se = min(sb + 32, min(l + 32 * i + 31, k));  // s < the chunk's largest t
           real acc = NINF;
           int base = tri_row(sb, k) + tt - sb - 1;  // E(sb, tt); row s+1 starts k-s-1 later
+          if (j < i) {
+            // every s of the tile is below every t: two s per three-operand max
+            int s = sb;
+#pragma unroll 2
+            for (; s + 1 < se; s += 2) {
+              const int b1 = base + k - s - 1;
+              acc = mid_max3(acc, Rp[s] - Et[base], Rp[s + 1] - Et[b1]);
+              base = b1 + k - s - 2;
+            }
+            if (s < se) acc = BT::max(acc, Rp[s] - Et[base]);
+          } else {
 #pragma unroll 4
-          for (int s = sb; s < se; ++s) {
-            const real v = Rp[s] - Et[base];
-            if (s < t) acc = BT::max(acc, v);
-            base += k - s - 1;
+            for (int s = sb; s < se; ++s) {
+              const real v = Rp[s] - Et[base];
+              if (s < t) acc = BT::max(acc, v);
+              base += k - s - 1;
+            }
           }
           if (t <= k && acc != NINF) atomicMin(&Rc[t], BT::of(acc));
         }
