@@ -87,30 +87,16 @@ __device__ inline int block_exclusive_scan(int* a, int n, int* tmp) {
 // Writes the row starts bounds[0..yhat] (bounds[yhat] = n) and returns yhat.
 // Works on shared or global arrays (generic pointers).
 // ---------------------------------------------------------------------------
-// Multipliers for exact division by small divisors: for 2 <= d < kMagicN,
-// magic[d] = ceil(2^32 / d), and floor(x / d) = umulhi(x, magic[d]) for every
-// 0 <= x < 2^16 (the error x * (magic[d] - 2^32/d) / 2^32 stays below 1/d).
-constexpr int kMagicN = 1024;
-__device__ __forceinline__ unsigned magic_of(int d) {
-  return (unsigned)(((1ull << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d);
-}
-
 template <typename GS, typename GRP, typename OUT>
 __device__ inline int equipartition_bounds_t(const GS* gs, const GRP* grp, int G, int n, int Y,
-                                             OUT* bounds, const unsigned* magic = nullptr) {
+                                             OUT* bounds) {
   // n <= 2^29, so every quantity below fits 32-bit integers
   int R0 = 0, g0 = 0, row = 1;
   bounds[0] = 0;
   while (true) {
     const int mult = Y - row + 1;
     const int thr = 2 * (n - R0);
-    const int num = thr + mult - 1;  // ceil(thr / mult) = floor(num / mult)
-    int qd;
-    if (magic && mult >= 2 && mult < kMagicN && num < 65536)
-      qd = (int)__umulhi((unsigned)num, magic[mult]);
-    else
-      qd = num / mult;
-    const int Tp = 2 * R0 + qd;
+    const int Tp = 2 * R0 + (thr + mult - 1) / mult;
     int ps = (Tp - 1) >> 1;
     if (ps > n - 1) ps = n - 1;
     int gc = (int)grp[ps];
@@ -134,11 +120,7 @@ __device__ inline int equipartition_bounds(const int* gs, const int* grp, int G,
   return equipartition_bounds_t<int, int, int>(gs, grp, G, n, Y, bounds);
 }
 
-__device__ inline int equipartition_bounds_u16(const uint16_t* gs, const uint16_t* grp, int G,
-                                               int n, int Y, uint16_t* bounds,
-                                               const unsigned* magic) {
-  return equipartition_bounds_t<uint16_t, uint16_t, uint16_t>(gs, grp, G, n, Y, bounds, magic);
-}
+
 
 // khat = max(floor(c * floor(B / y)), 1) (Appendix item 7: khat = c x)
 __host__ __device__ __forceinline__ int khat_of(int B, int y, double c) {

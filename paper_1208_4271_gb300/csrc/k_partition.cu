@@ -26,7 +26,6 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_job;
   __shared__ int s_y;                    // next row count of the current (pair, o)
-  __shared__ unsigned s_magic[kMagicN];  // exact division by the row counts left
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   uint16_t* pi = reinterpret_cast<uint16_t*>(sm + P.off_pi);   // [n] U position -> V position
@@ -44,7 +43,6 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
   const int64_t C = P.chunk_pairs;
   const int R = P.eq.R;
   const int64_t st = P.rk.stride;
-  for (int d = threadIdx.x; d < kMagicN; d += blockDim.x) s_magic[d] = d >= 2 ? magic_of(d) : 0u;
   for (;;) {
     if (threadIdx.x == 0) {
       s_job = (long long)atomicAdd(P.queue, 1ull);
@@ -145,14 +143,47 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       if (lane == 0) cstart[nc] = (uint16_t)n;
       __syncwarp();
       // superclumps: EquipartitionYAxis over the clumps (Algorithm
-      // GetSuperclumpsPartition), one row after another in lane 0
+      // GetSuperclumpsPartition), one row after another
       const int khat = khat_of(B, y, P.c);
       int k;
       const bool superclump = nc > khat;
       if (superclump) {
-        int kk = 0;
-        if (lane == 0) kk = equipartition_bounds_u16(cstart, cgrp, nc, n, khat, scb, s_magic);
-        k = __shfl_sync(0xffffffffu, kk, 0);
+        // EquipartitionYAxis over the clumps (cstart[g] = P_g, cstart[nc] =
+        // n): with the current superclump starting at position R0 = P_g0 and
+        // being number `row`, the next one starts at the first clump g > g0
+        // with (P_g + P_{g+1} - 2 R0) (khat - row + 1) >= 2 (n - R0) (the
+        // exact integer form of 2# + |S| >= 2d); the left side grows with g,
+        // so the warp tests 32 clumps at a time and takes the first by ballot
+        int R0 = 0, g0 = 0, row = 1;
+        if (lane == 0) scb[0] = 0;
+        for (;;) {
+          const int mult = khat - row + 1;
+          const int rhs = 2 * (n - R0);
+          int found = -1, Pf = 0;
+          for (int gb = g0 + 1; gb < nc; gb += 32) {
+            const int g = gb + lane;
+            int Pg = 0;
+            bool ok = false;
+            if (g < nc) {
+              Pg = cstart[g];
+              ok = (Pg + (int)cstart[g + 1] - 2 * R0) * mult >= rhs;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (m) {
+              const int src = __ffs(m) - 1;
+              found = gb + src;
+              Pf = __shfl_sync(0xffffffffu, Pg, src);
+              break;
+            }
+          }
+          if (found < 0) break;  // the rest of the clumps form the last row
+          R0 = Pf;
+          g0 = found;
+          if (lane == 0) scb[row] = (uint16_t)R0;
+          ++row;
+        }
+        if (lane == 0) scb[row] = (uint16_t)n;
+        k = row;
       } else {
         for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
         k = nc;
