@@ -101,9 +101,15 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       if (ties)
         for (int w = lane; w < (GU + 31) / 32; w += 32) mixed[w] = 0u;
       __syncwarp();
-      // rows of the V-sorted positions, then of the U-sorted positions
-      for (int j = 0; j < yhat; ++j)
-        for (int p = eb[j] + lane; p < eb[j + 1]; p += 32) Qs[p] = (uint16_t)j;
+      // rows of the V-sorted positions (each lane's row only moves forward;
+      // eb[yhat] = n), then of the U-sorted positions
+      {
+        int r = 0;
+        for (int p = lane; p < n; p += 32) {
+          while (eb[r + 1] <= p) ++r;
+          Qs[p] = (uint16_t)r;
+        }
+      }
       __syncwarp();
       for (int m = lane; m < n; m += 32) q[m] = Qs[pi[m]];
       __syncwarp();
@@ -212,6 +218,28 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
       // prefix over superclumps, written to the record; row totals give H(Q)
       int32_t* rcum = rec + 6 + ks;
       double sL = 0.0;
+      if (yhat >= 8) {
+        // many rows: lanes over rows, each row's prefix in place (counts
+        // <= n < 2^16), row totals into eb (free after the fill), the
+        // record written coalesced; the L(total) loads side by side, summed
+        // in increasing r
+        for (int r = lane; r < yhat; r += 32) {
+          uint16_t* row = cnt + r * ks;
+          int run = 0;
+          for (int t = 0; t < ks; ++t) {
+            run += row[t];
+            row[t] = (uint16_t)run;
+          }
+          eb[r] = run;
+        }
+        __syncwarp();
+        for (int i = lane; i < yhat * ks; i += 32) rcum[i] = cnt[i];
+        for (int r0 = 0; r0 < yhat; r0 += 32) {
+          const double Lr = r0 + lane < yhat ? P.L64[eb[r0 + lane]] : 0.0;
+          const int nr = min(32, yhat - r0);
+          for (int j = 0; j < nr; ++j) sL += __shfl_sync(0xffffffffu, Lr, j);
+        }
+      } else
       for (int r = 0; r < yhat; ++r) {
         int carry = 0;
         for (int base = 0; base < ks; base += 32) {
