@@ -103,8 +103,8 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   const int64_t rbytes = (int64_t)(tb.kmax + 1) * S.LS * rs;
   const int64_t lbytes = (int64_t)(n + 1) * rs;
   // traceback scratch aliased on the X buffers once the DP is done
-  // (cuts of four paths per warp, I(l), l*(l))
-  const int64_t cuts_b = (4LL * 4 * NW * S.xmax + 15) & ~int64_t(15);
+  // (cuts of up to eight paths per warp, I(l), l*(l))
+  const int64_t cuts_b = (4LL * 8 * NW * S.xmax + 15) & ~int64_t(15);
   const int64_t I_b = (8LL * (S.xmax + 1) + 15) & ~int64_t(15);
   const int64_t lst_b = 4LL * (S.xmax + 1);
   S.off_I_rel = (int)cuts_b;

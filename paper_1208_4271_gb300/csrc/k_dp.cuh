@@ -446,10 +446,11 @@ k_dp(DPParams P, DPPlan S) {
         // R(k, l'), l' <= l (the first in increasing l'), from one warp scan;
         // then from (k, l*) at (t, lv) an s with R(s, lv-1) - E(s, t) equal
         // to R(t, lv) (an exact match exists: a maximum is one of its
-        // candidates), scanning down from t - 1.  Since E >= 0, an s with
-        // R(s, lv-1) below the target cannot match and its E is not formed.
-        // Each warp follows four paths at once, one per group of 8 lanes,
-        // largest l first; every path is then re-scored in double.
+        // candidates), scanning down from t - 1 (since E >= 0, an s with
+        // R(s, lv-1) below the target cannot match).  Each warp follows
+        // several paths at once, one per group of G lanes, largest l first,
+        // G as large as lets every path start in the first round; every path
+        // is then re-scored in double.
         int* lst = reinterpret_cast<int*>(sm + S.off_X + S.off_lst_rel);
         if (warp == 0) {
           real cbest = Rget(k, 1);
@@ -478,12 +479,18 @@ k_dp(DPParams P, DPPlan S) {
           }
         }
         __syncthreads();
-        const int grp = lane >> 3, sub = lane & 7;
-        int* gcut = cuts + (warp * 4 + grp) * S.xmax;
+        // paths per round: G lanes per path, the largest G that still gives
+        // every path a group in one round (at least 4 lanes per group)
         const int npaths = lmax - 1;  // levels 2..lmax
-        for (int base = warp * 4; base < npaths; base += NW * 4) {
+        int G = 32;
+        while (G > 4 && (32 / G) * NW < npaths) --G;
+        const int NG = 32 / G;  // groups per warp; lanes from NG * G on idle
+        const int grp = lane / G, sub = lane - grp * G;
+        const unsigned gmask = G == 32 ? 0xffffffffu : (1u << G) - 1u;
+        int* gcut = cuts + (warp * 8 + min(grp, 7)) * S.xmax;
+        for (int base = warp * NG; base < npaths; base += NW * NG) {
           const int pidx = base + grp;
-          const bool act = pidx < npaths;  // the same in the whole group
+          const bool act = grp < NG && pidx < npaths;  // the same in the whole group
           const int l = lmax - pidx;
           const int lstar = act ? lst[l] : 1;
           int lv = lstar, tcur = k, s0 = k - 1;
@@ -504,11 +511,12 @@ k_dp(DPParams P, DPPlan S) {
                                  : entropy_term<real>(Lt, sd, SW, yhat, s, tcur);
               hit = r >= target && r - e == target;
             }
-            const unsigned m = (__ballot_sync(0xffffffffu, hit) >> (8 * grp)) & 0xffu;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            const unsigned m = grp < NG ? (bal >> (G * grp)) & gmask : 0u;
             if (going) {
               int found = -1;
               if (m) found = s0 - (__ffs(m) - 1);
-              else if (s0 - 8 < lv - 1) found = lv - 1;  // unreachable: R(t,lv) is a candidate
+              else if (s0 - G < lv - 1) found = lv - 1;  // unreachable: R(t,lv) is a candidate
               if (found >= 0) {
                 if (sub == 0) gcut[lv - 2] = found;
                 tcur = found;
@@ -522,18 +530,18 @@ k_dp(DPParams P, DPPlan S) {
                   going = false;
                 }
               } else {
-                s0 -= 8;
+                s0 -= G;
               }
             }
           }
           __syncwarp();
           // -E(0,s_1) - E(s_1,s_2) - ... - E(s_{l*-1},k) in double: the
           // terms (column c, row r) spread over the group's lanes, all loads
-          // independent
+          // independent, summed by the group's first lane
           double part = 0.0;
           if (act) {
             const int nt = lstar * (yhat + 1);
-            for (int i = sub; i < nt; i += 8) {
+            for (int i = sub; i < nt; i += G) {
               const int c = i / (yhat + 1), r = i - c * (yhat + 1);
               const int a = c == 0 ? 0 : gcut[c - 1];
               const int bnd = c == lstar - 1 ? k : gcut[c];
@@ -542,14 +550,16 @@ k_dp(DPParams P, DPPlan S) {
               part += r == 0 ? -L : L;
             }
           }
-          part += __shfl_xor_sync(0xffffffffu, part, 4);
-          part += __shfl_xor_sync(0xffffffffu, part, 2);
-          part += __shfl_xor_sync(0xffffffffu, part, 1);
-          if (act && sub == 0) Iw[l] = HQ + part / (double)n;
+          double tot = part;
+          for (int j = 1; j < G; ++j) {
+            const double o = __shfl_sync(0xffffffffu, part, min(lane + j, 31));
+            if (sub + j < G) tot += o;
+          }
+          if (act && sub == 0) Iw[l] = HQ + tot / (double)n;
           if (act && P.trace.d_cuts) {
             // as l - 1 column ends: the l* - 1 cuts, then empty columns at k
             int32_t* dst = P.trace.d_cuts + trace_task * P.trace.cut_stride + (l - 2) * (l - 1) / 2;
-            for (int c = sub; c < l - 1; c += 8) dst[c] = c < lstar - 1 ? gcut[c] : k;
+            for (int c = sub; c < l - 1; c += G) dst[c] = c < lstar - 1 ? gcut[c] : k;
           }
           __syncwarp();
         }
