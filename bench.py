@@ -122,8 +122,11 @@ def workload(rank, n_vars):
     return V, P
 
 
-def oracle_sample(V, P, cpu_seconds, rng_seed=0):
-    """Time the FP64 CPU oracle on a bounded random sample of the pairs."""
+def oracle_sample(V, P, cpu_seconds, rng_seed=0, keep=None):
+    """Time the FP64 CPU oracle on a bounded random sample of the pairs.
+
+    With keep (a dict), the sampled pair indices and the oracle's statistics
+    are stored in it for the parity report."""
     import oracle
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(rng_seed)
@@ -132,13 +135,50 @@ def oracle_sample(V, P, cpu_seconds, rng_seed=0):
     oracle.score_batch(V, probe, ALPHA, C, nthreads=threads)
     rate = probe.shape[0] / max(time.perf_counter() - t0, 1e-6)
     m = int(min(P.shape[0], max(threads, rate * cpu_seconds)))
-    sample = P[rng.choice(P.shape[0], m, replace=False)]
+    idx = np.sort(rng.choice(P.shape[0], m, replace=False))
+    sample = P[idx]
     t0 = time.perf_counter()
-    oracle.score_batch(V, sample, ALPHA, C, nthreads=threads)
+    ref = oracle.score_batch(V, sample, ALPHA, C, nthreads=threads)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["idx"] = idx
+        keep["stats"] = ref["stats"]
     return {"value": m / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
             "sample": "%d random pairs of the %d-variable all-pairs workload (n=%d), "
                       "FP64 oracle, OpenMP over pairs, %.1f s" % (m, V.shape[0], V.shape[1], dt)}
+
+
+def error_summary(got, ref):
+    """Max and 99th-percentile absolute error per statistic (MIC, MAS, MEV, MCN)."""
+    out = {}
+    for j, name in enumerate(("mic", "mas", "mev", "mcn")):
+        e = np.abs(np.asarray(got[name], dtype=np.float64) - ref[:, j])
+        out[name] = {"max": float(e.max()) if e.size else None,
+                     "p99": float(np.percentile(e, 99)) if e.size else None}
+    return out
+
+
+def partition_flips(Vd, dev, nv):
+    """Fraction of tasks whose chosen partition differs between the FP32 path
+    and the plain FP64 path (whose partitions equal the oracle's), on all pairs
+    of the first nv variables."""
+    import torch
+    from paper_1208_4271_gb300 import gmine
+    Ps = torch.from_numpy(gmine_all_pairs(nv)).to(dev)
+    cuts = {}
+    for prec in (gmine.PLAIN_FP64, gmine.FP32_DP_FP64_RESCORE):
+        tr, tt = gmine.alloc_trace(Ps.shape[0], Vd.shape[1], ALPHA, C, device=dev)
+        gmine.compute_batch(Vd[:nv], Ps, ALPHA, C, prec, want_M=False, trace=tr)
+        torch.cuda.synchronize(dev)
+        cuts[prec] = (tt["k"].cpu().numpy(), tt["cuts"].cpu().numpy())
+        del tt
+    k64, c64 = cuts[gmine.PLAIN_FP64]
+    k32, c32 = cuts[gmine.FP32_DP_FP64_RESCORE]
+    live = (k64 >= 2) & (k32 == k64)
+    differ = np.any(c64[live] != c32[live], axis=1)
+    return {"tasks": int(live.sum()), "differing": int(differ.sum()),
+            "fraction": float(differ.mean()) if live.any() else 0.0,
+            "sample": "all %d pairs of the first %d variables" % (Ps.shape[0], nv)}
 
 
 def run_reference(args, rank, world):
@@ -301,8 +341,27 @@ def main():
         del wsh
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(V, P, args.cpu_seconds)
+        keep = {}
+        cpu = oracle_sample(V, P, args.cpu_seconds, keep=keep)
+        # parity of the timed step's FP32 scores on the oracle's sample, of the
+        # plain FP64 path on a sample of its subset, and the partition flips
+        s32 = gmine.scores_to_numpy(scores)
+        got = {k: s32[k][keep["idx"]] for k in ("mic", "mas", "mev", "mcn")}
+        parity = {"fp32_vs_oracle": error_summary(got, keep["stats"]),
+                  "fp32_sample_pairs": int(keep["idx"].size)}
+        if fp64 is not None:
+            import oracle
+            s64 = gmine.scores_to_numpy(sc64)
+            rng = np.random.default_rng(7)
+            Ps_np = gmine_all_pairs(min(args.fp64_vars, p))
+            i64 = np.sort(rng.choice(Ps_np.shape[0], min(300, Ps_np.shape[0]), replace=False))
+            ref64 = oracle.score_batch(V, Ps_np[i64], ALPHA, C, nthreads=os.cpu_count() or 1)
+            parity["fp64_vs_oracle"] = error_summary({k: s64[k][i64] for k in ("mic", "mas", "mev", "mcn")},
+                                                     ref64["stats"])
+            parity["fp64_sample_pairs"] = int(i64.size)
+        parity["partition_flips_fp32"] = partition_flips(Vd, dev, min(40, p))
 
     if rank != 0:
         return
@@ -336,7 +395,8 @@ def main():
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu,
+            "parity": parity}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
