@@ -65,6 +65,8 @@ int device_info(DeviceInfo* d) {
   return GMINE_OK;
 }
 
+int rank_smem(int64_t n);
+
 // Shape bounds of the tasks with row counts y in [ylo, yhi] of a batch with
 // n samples and parameters (B, c).
 struct TaskBounds {
@@ -232,6 +234,10 @@ struct Layout {
   DPGroup grp[kMaxDPGroups];
   PartPlan part;
   int part_ctas;
+  int64_t o_partscr;     // partition regions in global memory (large n), or -1
+  int64_t o_rankscr;     // sort keys in global memory (large n), or -1
+  int rank_ctas, rank_smem_bytes;
+  int64_t rank_scr_per_cta;
   int64_t rec_per_orient;
   int64_t cells_max;
   int64_t o_Btab, o_L64, o_L32, o_lnt, o_recoff, o_nf;
@@ -292,7 +298,7 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   if (gmine_check_param(param) != GMINE_OK) return GMINE_E_PARAM;
   if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
   if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
-  if (n > kMaxRankN) return GMINE_E_LIMIT;
+  if (n > kMaxN) return GMINE_E_LIMIT;
   DeviceInfo dev;
   int rc = device_info(&dev);
   if (rc != GMINE_OK) return rc;
@@ -432,15 +438,30 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   }
   L->part = make_part_plan((int)n, L->tb, 4);
   if (L->part.total + 1024 > dev.smem_optin) L->part = make_part_plan((int)n, L->tb, 1);
-  if (L->part.total + 1024 > dev.smem_optin) return GMINE_E_LIMIT;
+  const bool part_global = L->part.total + 1024 > dev.smem_optin;
+  if (part_global) L->part = make_part_plan((int)n, L->tb, 4);  // in global scratch
   {
     int pb = 0;
-    const int smem = L->part.total;
+    const int smem = part_global ? 0 : L->part.total;
     cudaError_t e = cudaFuncSetAttribute(k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_partition, 32 * L->part.warps, smem);
     if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
     if (pb < 1) return GMINE_E_LIMIT;
-    L->part_ctas = pb * dev.sms;
+    L->part_ctas = (part_global ? std::min(pb, 4) : pb) * dev.sms;
+  }
+  // the sort: in shared memory up to kMaxRankN samples, else keys and indices
+  // in global scratch, two resident CTAs per SM looping over the slots
+  {
+    int64_t N2 = 1;
+    while (N2 < n) N2 <<= 1;
+    L->rank_smem_bytes = rank_smem(n);
+    L->rank_ctas = 0;
+    L->rank_scr_per_cta = 0;
+    if (L->rank_smem_bytes > dev.smem_optin) {
+      L->rank_smem_bytes = 4 * (kRankThreads + 1) + 64;
+      L->rank_ctas = 2 * dev.sms;
+      L->rank_scr_per_cta = (N2 * 12 + 255) & ~int64_t(255);
+    }
   }
   L->rec_per_orient = std::max<int64_t>(rec_offset(B, (int)n, param->c, B / 2 + 1), 4);
   const int64_t rec_pair = 2 * L->rec_per_orient * 4;
@@ -458,6 +479,8 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
     o = align256(o + std::max<int64_t>(bytes, 1));
     return at;
   };
+  L->o_partscr = part_global ? take((int64_t)L->part_ctas * ((L->part.total + 255) & ~255)) : -1;
+  L->o_rankscr = L->rank_ctas > 0 ? take((int64_t)L->rank_ctas * L->rank_scr_per_cta) : -1;
   L->o_Btab = take(4 * (n + 1));
   L->o_L64 = take(8 * (n + 1));
   L->o_L32 = take(4 * (n + 1));
@@ -540,11 +563,13 @@ int rank_smem(int64_t n) {
 
 // B(m) = floor(m^alpha) for m = 0..n, written into the workspace.
 int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
-  // n <= kMaxRankN: the table fits a stack buffer (no heap allocation)
-  int32_t Bt[kMaxRankN + 1];
+  // one host buffer per thread, grown to the largest n seen (no device
+  // allocation); the copy from pageable memory returns once the data is
+  // staged, so the buffer can be reused at once
+  static thread_local std::vector<int32_t> Bt;
+  if ((int64_t)Bt.size() < L.n + 1) Bt.resize((size_t)L.n + 1);
   for (int64_t m = 0; m <= L.n; ++m) Bt[m] = m > 0 ? host_B(m, alpha) : 0;
-  // pageable source: the call returns after the data has been staged
-  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt, sizeof(int32_t) * (size_t)(L.n + 1),
+  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt.data(), sizeof(int32_t) * (size_t)(L.n + 1),
                           cudaMemcpyHostToDevice, st));
   return GMINE_OK;
 }
@@ -564,12 +589,15 @@ int prepare_variables(const double* d_vars, void* ws, const Layout& L, double al
     k_nonfinite<<<(unsigned)((L.p + 7) / 8), 256, 0, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf));
     GM_CUDA(cudaGetLastError());
     ++*launches;
-    const int smem = rank_smem(L.n);
+    const int smem = L.rank_smem_bytes;
     GM_CUDA(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PairPrep pp = pair_prep(ws, L);
-    k_rank<<<(unsigned)L.p, kRankThreads, smem, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf),
-                                                      nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0,
-                                                      rank_data(ws, L));
+    unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
+    const int64_t rgrid = rscr ? std::min<int64_t>(L.p, L.rank_ctas) : L.p;
+    k_rank<<<(unsigned)rgrid, kRankThreads, smem, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf),
+                                                        nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0,
+                                                        L.p, rank_data(ws, L), rscr,
+                                                        L.rank_scr_per_cta);
     GM_CUDA(cudaGetLastError());
     ++*launches;
     if (L.tb.R > 0) {
@@ -651,7 +679,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   if (rc != GMINE_OK) return rc;
 
   const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
-  const int rsmem = rank_smem(L.n);
+  const int rsmem = L.rank_smem_bytes;
   if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
   DPTiming tim;
   DPTiming* timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
@@ -664,9 +692,13 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
     GM_CUDA(cudaGetLastError());
     ++launches;
     // pairs with missing samples: compacted per-pair ranks and equipartitions
-    k_rank<<<(unsigned)(2 * C), kRankThreads, rsmem, st>>>(
-        d_vars, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp,
-        at<int32_t>(ws, L.o_Btab), L.p, rank_data(ws, L));
+    {
+      unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
+      const int64_t rgrid = rscr ? std::min<int64_t>(2 * C, L.rank_ctas) : 2 * C;
+      k_rank<<<(unsigned)rgrid, kRankThreads, rsmem, st>>>(
+          d_vars, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp,
+          at<int32_t>(ws, L.o_Btab), L.p, 2 * C, rank_data(ws, L), rscr, L.rank_scr_per_cta);
+    }
     GM_CUDA(cudaGetLastError());
     ++launches;
     if (L.tb.R > 0) {
@@ -705,8 +737,10 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
       Q.off_scb = L.part.off_scb;
       Q.off_mixed = L.part.off_mixed;
       Q.off_eb = L.part.off_eb;
+      Q.gscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
+      Q.gscr_per_cta = (L.part.total + 255) & ~255;
       GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
-      k_partition<<<L.part_ctas, 32 * L.part.warps, L.part.total, st>>>(Q);
+      k_partition<<<L.part_ctas, 32 * L.part.warps, Q.gscr ? 0 : L.part.total, st>>>(Q);
       GM_CUDA(cudaGetLastError());
       ++launches;
       // the dynamic program: large row counts... small row counts

@@ -11,6 +11,7 @@ namespace gm {
 
 constexpr int kWarp = 32;
 constexpr int kMaxRankN = 16384;  // largest slot sorted in shared memory
+constexpr int kMaxN = 65535;      // positions and counts are stored in 16 bits
 
 // ---------------------------------------------------------------------------
 // Ordering key of a double: unsigned integers compare like the doubles, -0.0
@@ -222,6 +223,8 @@ struct PartParams {
   int off_warps;       // first per-warp region
   int warp_smem;       // bytes of shared memory per warp
   int off_Qs, off_q, off_cgrp, off_cstart, off_scb, off_mixed, off_eb;  // within a warp region
+  unsigned char* gscr;   // when set, the regions above live here (per CTA), not in shared memory
+  int64_t gscr_per_cta;
 };
 
 struct DPParams {

@@ -23,7 +23,9 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
 }
 
 __global__ void __launch_bounds__(128) k_partition(PartParams P) {
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(16) unsigned char smd[];
+  // the CTA's regions: shared memory, or (large n) this CTA's global scratch
+  unsigned char* sm = P.gscr ? P.gscr + (int64_t)blockIdx.x * P.gscr_per_cta : smd;
   __shared__ long long s_job;
   __shared__ int s_y;                    // next row count of the current (pair, o)
   const int lane = threadIdx.x & 31;

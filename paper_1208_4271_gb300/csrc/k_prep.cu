@@ -85,11 +85,21 @@ __global__ void __launch_bounds__(1024)
 k_rank(const double* __restrict__ vars, int64_t p, int n,
        const int32_t* __restrict__ nf, const int32_t* __restrict__ pairs,
        int64_t pair0, PairPrep pp, const int32_t* __restrict__ Btab,
-       int64_t slot_base, RankData rk) {
+       int64_t slot_base, int64_t nslots, RankData rk, unsigned char* gscr,
+       int64_t gscr_per_cta) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t slot = slot_base + blockIdx.x;
   const int tid = threadIdx.x;
   const int T = blockDim.x;
+  int N2 = 1;
+  while (N2 < n) N2 <<= 1;
+  // keys and indices in shared memory, or (slots beyond the shared-memory
+  // sort) in this CTA's global scratch; the scan buffer stays in shared
+  unsigned char* kbase = gscr ? gscr + (int64_t)blockIdx.x * gscr_per_cta : smem;
+  uint64_t* key = reinterpret_cast<uint64_t*>(kbase);
+  int* idx = reinterpret_cast<int*>(key + N2);
+  int* tmp = gscr ? reinterpret_cast<int*>(smem) : idx + N2;  // T + 1 ints
+  for (int64_t sl = blockIdx.x; sl < nslots; sl += gridDim.x) {
+  const int64_t slot = slot_base + sl;
   const double* xv = nullptr;
   const double* yv = nullptr;
   int side = 0;
@@ -100,12 +110,12 @@ k_rank(const double* __restrict__ vars, int64_t p, int n,
         rk.nslot[slot] = 0;
         rk.ngroups[slot] = 0;
       }
-      return;
+      continue;
     }
     xv = vars + slot * (int64_t)n;
   } else {
     const int64_t d = (slot - p) / 2;
-    if (d >= *pp.ndirty) return;
+    if (d >= *pp.ndirty) continue;
     side = (int)((slot - p) % 2);
     pair_local = pp.dirty[d];
     const int32_t X = pairs[2 * (pair0 + pair_local)];
@@ -113,12 +123,7 @@ k_rank(const double* __restrict__ vars, int64_t p, int n,
     xv = vars + (int64_t)X * n;
     yv = vars + (int64_t)Y * n;
   }
-
-  int N2 = 1;
-  while (N2 < n) N2 <<= 1;
-  uint64_t* key = reinterpret_cast<uint64_t*>(smem);
-  int* idx = reinterpret_cast<int*>(key + N2);
-  int* tmp = idx + N2;  // T + 1 ints
+  __syncthreads();  // the previous slot's arrays are no longer read
 
   int m_used = n;
   if (slot < p) {
@@ -196,6 +201,7 @@ k_rank(const double* __restrict__ vars, int64_t p, int n,
     rk.ngroups[slot] = G;
     rk.nslot[slot] = m_used;
   }
+  }  // slots
 }
 
 // ---------------------------------------------------------------------------

@@ -16,7 +16,8 @@ __global__ void k_pair_prep(const int32_t* pairs, int64_t pair0, int64_t chunk,
                             const int32_t* Btab, PairPrep pp);
 __global__ void k_rank(const double* vars, int64_t p, int n, const int32_t* nf,
                        const int32_t* pairs, int64_t pair0, PairPrep pp,
-                       const int32_t* Btab, int64_t slot_base, RankData rk);
+                       const int32_t* Btab, int64_t slot_base, int64_t nslots, RankData rk,
+                       unsigned char* gscr, int64_t gscr_per_cta);
 __global__ void k_equi(int64_t slot_base, int64_t nslots, int64_t p,
                        const int32_t* Btab, const int32_t* ndirty, RankData rk,
                        EquiData eq);

@@ -84,3 +84,34 @@ def test_uneven_pairs_with_missing_samples(alpha, precision):
     tol = 1e-9 if precision == gmine.PLAIN_FP64 else 1e-4
     run = run_batch(V, P, alpha, 15.0, precision, trace=False)
     compare_pairs(V, P, run, alpha, 15.0, tol)
+
+
+@pytest.fixture(scope="module")
+def large_n_batch():
+    # n = 20000 (the largest n of the uneven workload): a clean pair, a pair
+    # whose second variable misses 15 % of the samples (compacted to about
+    # 17,000), and a tie-heavy pair (rounded values); n > 16,384 takes the
+    # sort and partition paths through global scratch
+    rng = np.random.default_rng(20000)
+    n = 20000
+    x = rng.random(n)
+    V = np.empty((6, n))
+    V[0] = x
+    V[1] = np.sin(6.0 * x) + 0.3 * rng.standard_normal(n)
+    V[2] = rng.random(n)
+    V[3] = V[2] ** 2 + 0.05 * rng.standard_normal(n)
+    V[3][rng.random(n) < 0.15] = np.nan
+    V[4] = np.round(rng.random(n) * 40.0)
+    V[5] = np.round(V[4] + 3.0 * rng.standard_normal(n))
+    P = np.array([[0, 1], [2, 3], [4, 5]], dtype=np.int32)
+    ref = oracle.score_batch(V, P, 0.6, 15.0, nthreads=0, want_M=True)
+    return V, P, ref
+
+
+@pytest.mark.parametrize("precision", [gmine.PLAIN_FP64, gmine.FP32_DP_FP64_RESCORE])
+def test_large_n_beyond_shared_memory_sort(large_n_batch, precision):
+    V, P, ref = large_n_batch
+    tol = 1e-9 if precision == gmine.PLAIN_FP64 else 1e-4
+    run = run_batch(V, P, 0.6, 15.0, precision, trace=False)
+    errs = compare_pairs(V, P, run, 0.6, 15.0, tol, ref=ref)
+    print("n = 20000 precision %d: %s" % (precision, errs))

@@ -187,7 +187,7 @@ def test_host_buffers_match_device_path():
 
 
 def test_largest_n_single_pair():
-    """The largest n of this build (16384 samples per variable, B = 337)."""
+    """The largest n sorted in shared memory (16384 samples per variable, B = 337)."""
     rng = np.random.default_rng(12)
     n = 16384
     x = rng.uniform(size=n)
