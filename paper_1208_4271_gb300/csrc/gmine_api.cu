@@ -443,8 +443,7 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   {
     int pb = 0;
     const int smem = part_global ? 0 : L->part.total;
-    cudaError_t e = cudaFuncSetAttribute(k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_partition, 32 * L->part.warps, smem);
+    cudaError_t e = partition_configure(part_global, smem, 32 * L->part.warps, &pb);
     if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
     if (pb < 1) return GMINE_E_LIMIT;
     L->part_ctas = (part_global ? std::min(pb, 4) : pb) * dev.sms;
@@ -590,15 +589,12 @@ int prepare_variables(const double* d_vars, void* ws, const Layout& L, double al
     GM_CUDA(cudaGetLastError());
     ++*launches;
     const int smem = L.rank_smem_bytes;
-    GM_CUDA(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PairPrep pp = pair_prep(ws, L);
     unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
     const int64_t rgrid = rscr ? std::min<int64_t>(L.p, L.rank_ctas) : L.p;
-    k_rank<<<(unsigned)rgrid, kRankThreads, smem, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf),
-                                                        nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0,
-                                                        L.p, rank_data(ws, L), rscr,
-                                                        L.rank_scr_per_cta);
-    GM_CUDA(cudaGetLastError());
+    GM_CUDA(rank_launch((int)rgrid, kRankThreads, smem, st, d_vars, L.p, n,
+                        at<int32_t>(ws, L.o_nf), nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0, L.p,
+                        rank_data(ws, L), rscr, L.rank_scr_per_cta));
     ++*launches;
     if (L.tb.R > 0) {
       const int64_t work = L.p * L.tb.R;
@@ -695,11 +691,10 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
     {
       unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
       const int64_t rgrid = rscr ? std::min<int64_t>(2 * C, L.rank_ctas) : 2 * C;
-      k_rank<<<(unsigned)rgrid, kRankThreads, rsmem, st>>>(
-          d_vars, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp,
-          at<int32_t>(ws, L.o_Btab), L.p, 2 * C, rank_data(ws, L), rscr, L.rank_scr_per_cta);
+      GM_CUDA(rank_launch((int)rgrid, kRankThreads, rsmem, st, d_vars, L.p, (int)L.n,
+                          at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp, at<int32_t>(ws, L.o_Btab),
+                          L.p, 2 * C, rank_data(ws, L), rscr, L.rank_scr_per_cta));
     }
-    GM_CUDA(cudaGetLastError());
     ++launches;
     if (L.tb.R > 0) {
       const int64_t work = 2 * C * L.tb.R;
@@ -740,7 +735,8 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
       Q.gscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
       Q.gscr_per_cta = (L.part.total + 255) & ~255;
       GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
-      k_partition<<<L.part_ctas, 32 * L.part.warps, Q.gscr ? 0 : L.part.total, st>>>(Q);
+      GM_CUDA(partition_launch(Q.gscr != nullptr, L.part_ctas, 32 * L.part.warps,
+                               Q.gscr ? 0 : L.part.total, st, Q));
       GM_CUDA(cudaGetLastError());
       ++launches;
       // the dynamic program: large row counts... small row counts

@@ -22,10 +22,13 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
   return (bm[g >> 5] >> (g & 31)) & 1u;
 }
 
-__global__ void __launch_bounds__(128) k_partition(PartParams P) {
+template <bool GLOBAL>
+__global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
   extern __shared__ __align__(16) unsigned char smd[];
   // the CTA's regions: shared memory, or (large n) this CTA's global scratch
-  unsigned char* sm = P.gscr ? P.gscr + (int64_t)blockIdx.x * P.gscr_per_cta : smd;
+  // (a template parameter, so that the shared instance keeps shared-memory
+  // addressing)
+  unsigned char* sm = GLOBAL ? P.gscr + (int64_t)blockIdx.x * P.gscr_per_cta : smd;
   __shared__ long long s_job;
   __shared__ int s_y;                    // next row count of the current (pair, o)
   const int lane = threadIdx.x & 31;
@@ -270,6 +273,22 @@ __global__ void __launch_bounds__(128) k_partition(PartParams P) {
     }
     __syncthreads();
   }
+}
+
+cudaError_t partition_configure(bool global, int smem, int threads, int* blocks_per_sm) {
+  auto k = global ? k_partition_t<true> : k_partition_t<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
+}
+
+cudaError_t partition_launch(bool global, int grid, int threads, int smem, cudaStream_t st,
+                             const PartParams& P) {
+  if (global)
+    k_partition_t<true><<<grid, threads, smem, st>>>(P);
+  else
+    k_partition_t<false><<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
 }
 
 }  // namespace gm

@@ -81,8 +81,9 @@ __global__ void k_pair_prep(const int32_t* __restrict__ pairs, int64_t pair0,
 // (s - p) / 2 of the chunk, over the samples where both of the pair's
 // variables are finite (compacted, 0-based).
 // ---------------------------------------------------------------------------
+template <bool GLOBAL>
 __global__ void __launch_bounds__(1024)
-k_rank(const double* __restrict__ vars, int64_t p, int n,
+k_rank_t(const double* __restrict__ vars, int64_t p, int n,
        const int32_t* __restrict__ nf, const int32_t* __restrict__ pairs,
        int64_t pair0, PairPrep pp, const int32_t* __restrict__ Btab,
        int64_t slot_base, int64_t nslots, RankData rk, unsigned char* gscr,
@@ -94,10 +95,10 @@ k_rank(const double* __restrict__ vars, int64_t p, int n,
   while (N2 < n) N2 <<= 1;
   // keys and indices in shared memory, or (slots beyond the shared-memory
   // sort) in this CTA's global scratch; the scan buffer stays in shared
-  unsigned char* kbase = gscr ? gscr + (int64_t)blockIdx.x * gscr_per_cta : smem;
+  unsigned char* kbase = GLOBAL ? gscr + (int64_t)blockIdx.x * gscr_per_cta : smem;
   uint64_t* key = reinterpret_cast<uint64_t*>(kbase);
   int* idx = reinterpret_cast<int*>(key + N2);
-  int* tmp = gscr ? reinterpret_cast<int*>(smem) : idx + N2;  // T + 1 ints
+  int* tmp = GLOBAL ? reinterpret_cast<int*>(smem) : idx + N2;  // T + 1 ints
   for (int64_t sl = blockIdx.x; sl < nslots; sl += gridDim.x) {
   const int64_t slot = slot_base + sl;
   const double* xv = nullptr;
@@ -202,6 +203,22 @@ k_rank(const double* __restrict__ vars, int64_t p, int n,
     rk.nslot[slot] = m_used;
   }
   }  // slots
+}
+
+cudaError_t rank_launch(int grid, int threads, int smem, cudaStream_t st, const double* vars,
+                        int64_t p, int n, const int32_t* nf, const int32_t* pairs, int64_t pair0,
+                        PairPrep pp, const int32_t* Btab, int64_t slot_base, int64_t nslots,
+                        RankData rk, unsigned char* gscr, int64_t gscr_per_cta) {
+  auto k = gscr ? k_rank_t<true> : k_rank_t<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (gscr)
+    k_rank_t<true><<<grid, threads, smem, st>>>(vars, p, n, nf, pairs, pair0, pp, Btab, slot_base,
+                                                nslots, rk, gscr, gscr_per_cta);
+  else
+    k_rank_t<false><<<grid, threads, smem, st>>>(vars, p, n, nf, pairs, pair0, pp, Btab, slot_base,
+                                                 nslots, rk, gscr, gscr_per_cta);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -14,15 +14,17 @@ __global__ void k_nonfinite(const double* vars, int64_t p, int n, int32_t* nf);
 __global__ void k_pair_prep(const int32_t* pairs, int64_t pair0, int64_t chunk,
                             int64_t p, int n, const int32_t* nf,
                             const int32_t* Btab, PairPrep pp);
-__global__ void k_rank(const double* vars, int64_t p, int n, const int32_t* nf,
-                       const int32_t* pairs, int64_t pair0, PairPrep pp,
-                       const int32_t* Btab, int64_t slot_base, int64_t nslots, RankData rk,
-                       unsigned char* gscr, int64_t gscr_per_cta);
+cudaError_t rank_launch(int grid, int threads, int smem, cudaStream_t st, const double* vars,
+                        int64_t p, int n, const int32_t* nf, const int32_t* pairs, int64_t pair0,
+                        PairPrep pp, const int32_t* Btab, int64_t slot_base, int64_t nslots,
+                        RankData rk, unsigned char* gscr, int64_t gscr_per_cta);
 __global__ void k_equi(int64_t slot_base, int64_t nslots, int64_t p,
                        const int32_t* Btab, const int32_t* ndirty, RankData rk,
                        EquiData eq);
 __global__ void k_equi_single(int64_t p, int y, RankData rk, EquiData eq);
-__global__ void k_partition(PartParams P);
+cudaError_t partition_configure(bool global, int smem, int threads, int* blocks_per_sm);
+cudaError_t partition_launch(bool global, int grid, int threads, int smem, cudaStream_t st,
+                             const PartParams& P);
 __global__ void k_final(FinalParams F);
 __global__ void k_rank_export(RankData rk, int64_t p, int32_t* rank_out,
                               int32_t* perm_out, int32_t* groups_out);
