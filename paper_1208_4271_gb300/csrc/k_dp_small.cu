@@ -53,38 +53,33 @@ __device__ __forceinline__ real E_small(const real* __restrict__ Lt, const int* 
   return e;
 }
 
-// E(s1,t1) and E(s2,t2) with their loads interleaved: two independent
+// E(s_q, t_q) for NE entries with their loads interleaved: NE independent
 // chains per lane, each in increasing r
-template <typename real>
-__device__ __forceinline__ void E_small2(const real* __restrict__ Lt, const int* __restrict__ scb,
-                                         const int* __restrict__ cum, int ks, int yhat, int s1, int t1,
-                                         int s2, int t2, real& e1, real& e2) {
-  real a = Lt[scb[t1] - scb[s1]];
-  real b = Lt[scb[t2] - scb[s2]];
-  const int* __restrict__ ct1 = cum + t1;
-  const int* __restrict__ cs1 = cum + s1;
-  const int* __restrict__ ct2 = cum + t2;
-  const int* __restrict__ cs2 = cum + s2;
+template <typename real, int NE>
+__device__ __forceinline__ void E_smallN(const real* __restrict__ Lt, const int* __restrict__ scb,
+                                         const int* __restrict__ cum, int ks, int yhat,
+                                         const int (&s)[NE], const int (&t)[NE], real (&e)[NE]) {
+#pragma unroll
+  for (int q = 0; q < NE; ++q) e[q] = Lt[scb[t[q]] - scb[s[q]]];
   int r = 0;
   for (; r + 4 <= yhat; r += 4) {
-    real la[4], lb[4];
+    real l[NE][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      la[q] = Lt[ct1[(r + q) * ks] - cs1[(r + q) * ks]];
-      lb[q] = Lt[ct2[(r + q) * ks] - cs2[(r + q) * ks]];
-    }
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a -= la[q];
-      b -= lb[q];
-    }
+      for (int q = 0; q < NE; ++q) l[q][u] = Lt[cum[(r + u) * ks + t[q]] - cum[(r + u) * ks + s[q]]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < NE; ++q) e[q] -= l[q][u];
   }
   for (; r < yhat; ++r) {
-    a -= Lt[ct1[r * ks] - cs1[r * ks]];
-    b -= Lt[ct2[r * ks] - cs2[r * ks]];
+    real l[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) l[q] = Lt[cum[r * ks + t[q]] - cum[r * ks + s[q]]];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) e[q] -= l[q];
   }
-  e1 = a;
-  e2 = b;
 }
 
 // offset of E(s, .) in the packed triangle: row s holds t = s+1 .. k
@@ -154,8 +149,8 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
 
     if (k >= 2) {
       // ---- the entropy triangle: entry f = tri_row(s,k) + t - s - 1 in
-      // lane f mod 32, two entries (f, f + 32) at a time, (s, t) advancing
-      // along the rows
+      // lane f mod 32, four entries (f, f + 32, ...) at a time, (s, t)
+      // advancing along the rows
       {
         const int npairs = k * (k + 1) / 2;
         int s = 0, pos = lane;  // pos = t - s - 1 within row s (k - s entries)
@@ -167,16 +162,21 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
           }
         };
         advance(0);
-        for (int f = lane; f < npairs; f += 64) {
-          const int s1 = s, t1 = s + 1 + pos;
-          advance(32);
-          const bool two = f + 32 < npairs;
-          const int s2 = two ? s : s1, t2 = two ? s + 1 + pos : t1;
-          real e1, e2;
-          E_small2<real>(Lt, scb, cum, ks, yhat, s1, t1, s2, t2, e1, e2);
-          Et[f] = e1;
-          if (two) Et[f + 32] = e2;
-          advance(32);
+        constexpr int NE = 4;  // entries in flight per lane
+        for (int f = lane; f < npairs; f += 32 * NE) {
+          int sq[NE], tq[NE];
+#pragma unroll
+          for (int q = 0; q < NE; ++q) {
+            const bool live = f + 32 * q < npairs;
+            sq[q] = live ? s : sq[0];
+            tq[q] = live ? s + 1 + pos : tq[0];
+            advance(32);
+          }
+          real e[NE];
+          E_smallN<real, NE>(Lt, scb, cum, ks, yhat, sq, tq, e);
+#pragma unroll
+          for (int q = 0; q < NE; ++q)
+            if (f + 32 * q < npairs) Et[f + 32 * q] = e[q];
         }
       }
       __syncwarp();
