@@ -62,7 +62,8 @@ extern "C" {
 #define GMINE_E_ARG 5        /* NULL pointer, negative size, bad index */
 #define GMINE_E_WORKSPACE 6  /* workspace smaller than gmine_plan reported */
 #define GMINE_E_CUDA 7       /* a CUDA runtime call failed */
-#define GMINE_E_LIMIT 8      /* a size beyond what this build supports (n > 65535) */
+#define GMINE_E_LIMIT 8      /* a size beyond what this build supports (n > 131072; the plain FP64
+                                path above 65535 samples) */
 #define GMINE_E_NODEVICE 9   /* no usable CUDA device */
 
 /* precision of the OptimizeXAxis dynamic program */

@@ -118,10 +118,20 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   S.off_Eb = add((int64_t)32 * 33 * rs);
   S.off_rbuf = add((int64_t)2 * 32 * rs);
   S.off_Rtop = add((int64_t)(tb.kmax + 1) * rs);
-  S.off_sd = add(4LL * std::max(tb.sd_max, 4));
+  const int64_t sdbytes = 4LL * std::max(tb.sd_max, 4);
+  const int64_t before_sd = fixed;
+  S.off_sd = add(sdbytes);
+  S.sd_scr_off = -1;
   const int reserve = 1024;
   const bool in_smem = fixed + rbytes + lbytes + 32 + reserve <= smem_optin;
   *r_in_smem = in_smem;
+  if (!in_smem && fixed + reserve > smem_optin) {
+    // the superclump rows do not fit beside the X rows either (very large
+    // k): they go to the CTA's global scratch after the R table
+    fixed = before_sd;
+    S.off_sd = -1;
+    S.sd_scr_off = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+  }
   int64_t o = fixed;
   if (in_smem) {
     S.off_L = (int)o;
@@ -146,17 +156,18 @@ struct PartPlan {
 PartPlan make_part_plan(int n, const TaskBounds& tb, int warps) {
   PartPlan pp{};
   pp.warps = warps;
+  const int64_t es = n > kMaxN16 ? 4 : 2;  // bytes per position (and count)
   int o = 0;
   auto add = [&](int64_t b) { const int at = o; o = (int)((o + b + 15) & ~int64_t(15)); return at; };
-  pp.off_pi = add(2LL * n);
-  pp.off_gU = add(2LL * n);
+  pp.off_pi = add(es * n);
+  pp.off_gU = add(es * n);
   pp.off_warps = o;
   o = 0;
-  pp.off_Qs = add(std::max<int64_t>(2LL * n, 2LL * std::max(tb.cum_max, 1) + 4));  // Qs, then counts
-  pp.off_q = add(2LL * n);
-  pp.off_cgrp = add(2LL * n);
-  pp.off_cstart = add(2LL * (n + 1));
-  pp.off_scb = add(2LL * (tb.kmax + 1));
+  pp.off_Qs = add(std::max<int64_t>(es * n, es * std::max(tb.cum_max, 1) + 4));  // Qs, then counts
+  pp.off_q = add(es * n);
+  pp.off_cgrp = add(es * n);
+  pp.off_cstart = add(es * (n + 1));
+  pp.off_scb = add(es * (tb.kmax + 1));
   pp.off_mixed = add(4LL * ((n + 31) / 32 + 1));
   pp.off_eb = add(4LL * (tb.B / 2 + 2));
   pp.warp_smem = o;
@@ -235,6 +246,7 @@ struct Layout {
   PartPlan part;
   int part_ctas;
   int64_t o_partscr;     // partition regions in global memory (large n), or -1
+  bool part_wide;        // 32-bit positions in the partition (n > 65535)
   int64_t o_rankscr;     // sort keys in global memory (large n), or -1
   int rank_ctas, rank_smem_bytes;
   int64_t rank_scr_per_cta;
@@ -257,8 +269,11 @@ int dp_occupancy(bool fp32, bool rsm, int lev, int smem, int threads, int* block
 
 int64_t dp_scratch(const TaskBounds& tb, const DPPlan& S, bool fp32, bool r_smem) {
   const int rs = fp32 ? 4 : 8;
-  // one spare row: a level group may read past the last row's columns
-  return r_smem ? 0 : align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+  // one spare row: a level group may read past the last row's columns;
+  // then the superclump rows when they do not fit in shared memory
+  if (r_smem) return 0;
+  const int64_t r = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+  return S.off_sd < 0 ? align256(r + 4LL * std::max(tb.sd_max, 4)) : r;
 }
 
 // CUDA events around the DP launches of one call (h_dp_ms of gmine_trace).
@@ -343,13 +358,17 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       while (g.threads > 32 && g.off_two_rec + g.threads / 32 * g.two_rec_bytes + 1024 > dev.smem_optin)
         g.threads /= 2;
       g.smem_two = g.off_two_rec + g.threads / 32 * g.two_rec_bytes;
-      if (g.smem_two + 1024 > dev.smem_optin) return GMINE_E_LIMIT;
-      cudaError_t e = dp_two_configure(fp32, g.smem_two, g.threads, &blocks);
-      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
-      if (blocks < 1) return GMINE_E_LIMIT;
-      g.ctas = blocks * dev.sms;
-      g.scratch_per_cta = 0;
-      continue;
+      if (g.smem_two + 1024 <= dev.smem_optin) {
+        cudaError_t e = dp_two_configure(fp32, g.smem_two, g.threads, &blocks);
+        if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+        if (blocks < 1) return GMINE_E_LIMIT;
+        g.ctas = blocks * dev.sms;
+        g.scratch_per_cta = 0;
+        continue;
+      }
+      // the table does not fit (very large n): the general kernels take it
+      g.two = false;
+      g.lev = dp_level_group(fp32, 1);
     }
     if (g.lev >= 8 && g.lev <= 12) {
       // few levels, entropy triangle small enough for two CTAs per SM:
@@ -438,12 +457,14 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   }
   L->part = make_part_plan((int)n, L->tb, 4);
   if (L->part.total + 1024 > dev.smem_optin) L->part = make_part_plan((int)n, L->tb, 1);
-  const bool part_global = L->part.total + 1024 > dev.smem_optin;
+  const bool part_wide = n > kMaxN16;  // 32-bit positions and counts
+  const bool part_global = part_wide || L->part.total + 1024 > dev.smem_optin;
   if (part_global) L->part = make_part_plan((int)n, L->tb, 4);  // in global scratch
+  L->part_wide = part_wide;
   {
     int pb = 0;
     const int smem = part_global ? 0 : L->part.total;
-    cudaError_t e = partition_configure(part_global, smem, 32 * L->part.warps, &pb);
+    cudaError_t e = partition_configure(part_global, part_wide, smem, 32 * L->part.warps, &pb);
     if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
     if (pb < 1) return GMINE_E_LIMIT;
     L->part_ctas = (part_global ? std::min(pb, 4) : pb) * dev.sms;
@@ -735,7 +756,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
       Q.gscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
       Q.gscr_per_cta = (L.part.total + 255) & ~255;
       GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
-      GM_CUDA(partition_launch(Q.gscr != nullptr, L.part_ctas, 32 * L.part.warps,
+      GM_CUDA(partition_launch(Q.gscr != nullptr, L.part_wide, L.part_ctas, 32 * L.part.warps,
                                Q.gscr ? 0 : L.part.total, st, Q));
       GM_CUDA(cudaGetLastError());
       ++launches;

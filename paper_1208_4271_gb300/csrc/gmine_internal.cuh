@@ -11,7 +11,8 @@ namespace gm {
 
 constexpr int kWarp = 32;
 constexpr int kMaxRankN = 16384;  // largest slot sorted in shared memory
-constexpr int kMaxN = 65535;      // positions and counts are stored in 16 bits
+constexpr int kMaxN = 131072;     // largest n (the global-memory sort's scratch per CTA)
+constexpr int kMaxN16 = 65535;    // positions and counts fit 16 bits up to here
 
 // ---------------------------------------------------------------------------
 // Ordering key of a double: unsigned integers compare like the doubles, -0.0
@@ -269,6 +270,7 @@ struct MidPlan {
 // Shared-memory layout of the DP kernel (byte offsets).
 struct DPPlan {
   int off_R, off_Rtop, off_X, off_Eb, off_rbuf, off_L, off_sd;
+  int64_t sd_scr_off;  // off_sd < 0: the superclump rows live in the CTA's global scratch here
   int off_I_rel, off_lst_rel;  // traceback scratch inside the X region
   int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4
   int LX;     // row stride of the X buffers: levels 1..lmax, odd (the lanes'

@@ -322,7 +322,11 @@ k_dp(DPParams P, DPPlan S) {
   U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // [32][33]
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
-  int* sd = reinterpret_cast<int*>(sm + S.off_sd);        // [kmax+1][SW]
+  // [kmax+1][SW]: shared memory, or (global R table, very large k) after
+  // the R table in the CTA's scratch
+  int* sd = (!RSM && S.off_sd < 0)
+                ? reinterpret_cast<int*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.sd_scr_off)
+                : reinterpret_cast<int*>(sm + S.off_sd);
   // after the DP the X buffers hold the traceback scratch
   int* cuts = reinterpret_cast<int*>(sm + S.off_X);                       // [4 NW][xmax]
   double* Iw = reinterpret_cast<double*>(sm + S.off_X + S.off_I_rel);     // [xmax+1]

@@ -22,7 +22,7 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
   return (bm[g >> 5] >> (g & 31)) & 1u;
 }
 
-template <bool GLOBAL>
+template <bool GLOBAL, typename IT>
 __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
   extern __shared__ __align__(16) unsigned char smd[];
   // the CTA's regions: shared memory, or (large n) this CTA's global scratch
@@ -33,15 +33,15 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
   __shared__ int s_y;                    // next row count of the current (pair, o)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint16_t* pi = reinterpret_cast<uint16_t*>(sm + P.off_pi);   // [n] U position -> V position
-  uint16_t* gU = reinterpret_cast<uint16_t*>(sm + P.off_gU);   // [n] U position -> tie group
+  IT* pi = reinterpret_cast<IT*>(sm + P.off_pi);   // [n] U position -> V position
+  IT* gU = reinterpret_cast<IT*>(sm + P.off_gU);   // [n] U position -> tie group
   unsigned char* my = sm + P.off_warps + (int64_t)wib * P.warp_smem;
-  uint16_t* Qs = reinterpret_cast<uint16_t*>(my + P.off_Qs);     // V position -> row
-  uint16_t* cnt = reinterpret_cast<uint16_t*>(my + P.off_Qs);    // counts (aliases Qs)
-  uint16_t* q = reinterpret_cast<uint16_t*>(my + P.off_q);       // U position -> row
-  uint16_t* cgrp = reinterpret_cast<uint16_t*>(my + P.off_cgrp); // U position -> clump
-  uint16_t* cstart = reinterpret_cast<uint16_t*>(my + P.off_cstart);
-  uint16_t* scb = reinterpret_cast<uint16_t*>(my + P.off_scb);
+  IT* Qs = reinterpret_cast<IT*>(my + P.off_Qs);     // V position -> row
+  IT* cnt = reinterpret_cast<IT*>(my + P.off_Qs);    // counts (aliases Qs)
+  IT* q = reinterpret_cast<IT*>(my + P.off_q);       // U position -> row
+  IT* cgrp = reinterpret_cast<IT*>(my + P.off_cgrp); // U position -> clump
+  IT* cstart = reinterpret_cast<IT*>(my + P.off_cstart);
+  IT* scb = reinterpret_cast<IT*>(my + P.off_scb);
   uint32_t* mixed = reinterpret_cast<uint32_t*>(my + P.off_mixed);
   int* eb = reinterpret_cast<int*>(my + P.off_eb);
 
@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
     const int32_t* grpU = P.rk.grp + (int64_t)sU * st;
     const int GU = P.rk.ngroups[sU];
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      pi[m] = (uint16_t)posV[permU[m]];
-      gU[m] = (uint16_t)grpU[m];
+      pi[m] = (IT)posV[permU[m]];
+      gU[m] = (IT)grpU[m];
     }
     __syncthreads();
 
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
         int r = 0;
         for (int p = lane; p < n; p += 32) {
           while (eb[r + 1] <= p) ++r;
-          Qs[p] = (uint16_t)r;
+          Qs[p] = (IT)r;
         }
       }
       __syncwarp();
@@ -146,12 +146,12 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
         const unsigned mask = __ballot_sync(0xffffffffu, f);
         const int before = __popc(mask & ((1u << lane) - 1u));
         if (m < n) {
-          cgrp[m] = (uint16_t)(nc + before + (f ? 1 : 0) - 1);
-          if (f) cstart[nc + before] = (uint16_t)m;
+          cgrp[m] = (IT)(nc + before + (f ? 1 : 0) - 1);
+          if (f) cstart[nc + before] = (IT)m;
         }
         nc += __popc(mask);
       }
-      if (lane == 0) cstart[nc] = (uint16_t)n;
+      if (lane == 0) cstart[nc] = (IT)n;
       __syncwarp();
       // superclumps: EquipartitionYAxis over the clumps (Algorithm
       // GetSuperclumpsPartition), one row after another
@@ -190,10 +190,10 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
           if (found < 0) break;  // the rest of the clumps form the last row
           R0 = Pf;
           g0 = found;
-          if (lane == 0) scb[row] = (uint16_t)R0;
+          if (lane == 0) scb[row] = (IT)R0;
           ++row;
         }
-        if (lane == 0) scb[row] = (uint16_t)n;
+        if (lane == 0) scb[row] = (IT)n;
         k = row;
       } else {
         for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
@@ -203,21 +203,26 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       __syncwarp();
       // superclump of every clump (cstart is free once the superclumps are
       // known): a clump lies inside one superclump
-      uint16_t* sc_of = cstart;
+      IT* sc_of = cstart;
       if (superclump) {
         for (int t = lane; t < k; t += 32) {
           const int c0 = cgrp[scb[t]], c1 = cgrp[scb[t + 1] - 1];
-          for (int c = c0; c <= c1; ++c) sc_of[c] = (uint16_t)t;
+          for (int c = c0; c <= c1; ++c) sc_of[c] = (IT)t;
         }
       }
-      // counts, 16 bits each (n < 65536), two per 32-bit word
-      for (int i = lane; i < (yhat * ks + 1) / 2; i += 32) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
+      // counts: 16 bits each, two per 32-bit word (n < 65536), or 32 bits
+      constexpr int per_word = 4 / (int)sizeof(IT);
+      for (int i = lane; i < (yhat * ks + per_word - 1) / per_word; i += 32)
+        reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
       __syncwarp();
       for (int m = lane; m < n; m += 32) {
         const int c = cgrp[m];
         const int t = superclump ? (int)sc_of[c] : c;
         const int i = (int)q[m] * ks + t + 1;
-        atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (i >> 1), 1u << (16 * (i & 1)));
+        if constexpr (sizeof(IT) == 2)
+          atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (i >> 1), 1u << (16 * (i & 1)));
+        else
+          atomicAdd(reinterpret_cast<uint32_t*>(cnt) + i, 1u);
       }
       __syncwarp();
       // prefix over superclumps, written to the record; row totals give H(Q)
@@ -225,15 +230,15 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       double sL = 0.0;
       if (yhat >= 8) {
         // many rows: lanes over rows, each row's prefix in place (counts
-        // <= n < 2^16), row totals into eb (free after the fill), the
+        // <= n fit the index type), row totals into eb (free after the fill), the
         // record written coalesced; the L(total) loads side by side, summed
         // in increasing r
         for (int r = lane; r < yhat; r += 32) {
-          uint16_t* row = cnt + r * ks;
+          IT* row = cnt + r * ks;
           int run = 0;
           for (int t = 0; t < ks; ++t) {
             run += row[t];
-            row[t] = (uint16_t)run;
+            row[t] = (IT)run;
           }
           eb[r] = run;
         }
@@ -275,19 +280,22 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
   }
 }
 
-cudaError_t partition_configure(bool global, int smem, int threads, int* blocks_per_sm) {
-  auto k = global ? k_partition_t<true> : k_partition_t<false>;
+cudaError_t partition_configure(bool global, bool wide, int smem, int threads, int* blocks_per_sm) {
+  auto k = wide ? k_partition_t<true, uint32_t>
+                : (global ? k_partition_t<true, uint16_t> : k_partition_t<false, uint16_t>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 
-cudaError_t partition_launch(bool global, int grid, int threads, int smem, cudaStream_t st,
-                             const PartParams& P) {
-  if (global)
-    k_partition_t<true><<<grid, threads, smem, st>>>(P);
+cudaError_t partition_launch(bool global, bool wide, int grid, int threads, int smem,
+                             cudaStream_t st, const PartParams& P) {
+  if (wide)
+    k_partition_t<true, uint32_t><<<grid, threads, smem, st>>>(P);
+  else if (global)
+    k_partition_t<true, uint16_t><<<grid, threads, smem, st>>>(P);
   else
-    k_partition_t<false><<<grid, threads, smem, st>>>(P);
+    k_partition_t<false, uint16_t><<<grid, threads, smem, st>>>(P);
   return cudaGetLastError();
 }
 

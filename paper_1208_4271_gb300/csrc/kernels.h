@@ -22,9 +22,9 @@ __global__ void k_equi(int64_t slot_base, int64_t nslots, int64_t p,
                        const int32_t* Btab, const int32_t* ndirty, RankData rk,
                        EquiData eq);
 __global__ void k_equi_single(int64_t p, int y, RankData rk, EquiData eq);
-cudaError_t partition_configure(bool global, int smem, int threads, int* blocks_per_sm);
-cudaError_t partition_launch(bool global, int grid, int threads, int smem, cudaStream_t st,
-                             const PartParams& P);
+cudaError_t partition_configure(bool global, bool wide, int smem, int threads, int* blocks_per_sm);
+cudaError_t partition_launch(bool global, bool wide, int grid, int threads, int smem,
+                             cudaStream_t st, const PartParams& P);
 __global__ void k_final(FinalParams F);
 __global__ void k_rank_export(RankData rk, int64_t p, int32_t* rank_out,
                               int32_t* perm_out, int32_t* groups_out);

@@ -115,3 +115,35 @@ def test_large_n_beyond_shared_memory_sort(large_n_batch, precision):
     run = run_batch(V, P, 0.6, 15.0, precision, trace=False)
     errs = compare_pairs(V, P, run, 0.6, 15.0, tol, ref=ref)
     print("n = 20000 precision %d: %s" % (precision, errs))
+
+
+def test_n_100000_properties():
+    """n = 100,000 (B = 999, up to 7,485 superclumps): the FP32 path, checked
+    by properties that hold at any size (the oracle is too slow here): MIC = 1
+    for a noiseless monotone pair, 0 <= M-statistics <= 1, MEV <= MIC,
+    MCN = log2(mcn_xy), 5,056 cells, and bitwise-identical scores after a
+    permutation of the samples. The plain FP64 path reports GMINE_E_LIMIT at
+    this size."""
+    rng = np.random.default_rng(100000)
+    n = 100000
+    x = rng.random(n)
+    V = np.stack([x, np.exp(3.0 * x), rng.random(n), np.zeros(n)])
+    V[3] = np.sin(6.0 * V[2]) + 0.3 * rng.standard_normal(n)
+    P = np.array([[0, 1], [2, 3]], dtype=np.int32)
+    run = run_batch(V, P, 0.6, 15.0, gmine.FP32_DP_FP64_RESCORE, trace=False, want_M=True)
+    s = run["scores"]
+    assert np.all(s["status"] == gmine.OK)
+    assert np.all(s["n_used"] == n) and np.all(s["B"] == 999) and np.all(s["m_cells"] == 5056)
+    assert abs(s["mic"][0] - 1.0) <= 1e-9
+    for key in ("mic", "mas", "mev"):
+        assert np.all(s[key] >= 0.0) and np.all(s[key] <= 1.0 + 1e-9)
+    assert np.all(s["mev"] <= s["mic"] + 1e-12)
+    assert np.allclose(s["mcn"], np.log2(s["mcn_xy"]), rtol=0, atol=1e-12)
+    perm = rng.permutation(n)
+    run2 = run_batch(V[:, perm], P, 0.6, 15.0, gmine.FP32_DP_FP64_RESCORE, trace=False, want_M=True)
+    for key in ("mic", "mas", "mev", "mcn"):
+        assert np.array_equal(s[key], run2["scores"][key]), key
+    assert np.array_equal(run["M"], run2["M"])
+    print("n = 100000: MIC %.6f %.6f, MAS %.6f, MCN %.3f" % (s["mic"][0], s["mic"][1], s["mas"][1], s["mcn"][1]))
+    with pytest.raises(gmine.GmineError):
+        run_batch(V, P, 0.6, 15.0, gmine.PLAIN_FP64, trace=False, want_M=False)
