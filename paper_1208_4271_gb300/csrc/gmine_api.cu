@@ -14,12 +14,10 @@ using namespace gm;
 
 namespace {
 
-constexpr int kTaskThreads = 256;
-constexpr int64_t kChunkPairs = 32768;
+constexpr int64_t kChunkPairs = 32768;  // largest chunk of pairs per pass
 constexpr int kRankThreads = 1024;
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
-int align16i(int64_t b) { return (int)((b + 15) & ~int64_t(15)); }
 
 #define GM_CUDA(call)                                          \
   do {                                                         \
@@ -485,7 +483,7 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   }
   L->rec_per_orient = std::max<int64_t>(rec_offset(B, (int)n, param->c, B / 2 + 1), 4);
   const int64_t rec_pair = 2 * L->rec_per_orient * 4;
-  L->chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n_pairs, 32768),
+  L->chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n_pairs, kChunkPairs),
                                                     kRecBudget / rec_pair));
   L->slots = p + 2 * L->chunk;
   L->cells_max = std::max<int64_t>(host_cells(B), 1);
