@@ -113,9 +113,9 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   int64_t fixed = 0;
   auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
   S.off_X = add(xbytes);
-  S.off_Eb = add((int64_t)32 * 33 * rs);
+  S.off_Eb = add((int64_t)(32 * 31 / 2) * rs);  // the in-block triangle
   S.off_rbuf = add((int64_t)2 * 32 * rs);
-  S.off_Rtop = add((int64_t)(tb.kmax + 1) * rs);
+  S.off_Rtop = add((int64_t)rs);  // R(k, lmax)
   const int64_t sdbytes = 4LL * std::max(tb.sd_max, 4);
   const int64_t before_sd = fixed;
   S.off_sd = add(sdbytes);

@@ -266,7 +266,7 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
   else pinf = __longlong_as_double(0x7ff0000000000000ll);
   real ec[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) ec[i] = (tv && i < lane) ? Eb[i * 33 + lane] : pinf;
+  for (int i = 0; i < 32; ++i) ec[i] = (tv && i < lane) ? Eb[lane * (lane - 1) / 2 + i] : pinf;
   real rcur = tv ? Rt[t * LS] : BT::ninf();  // level 1
   const typename Bits<real>::U* xr = Xcur + lane * LX;
   int par = 0;
@@ -291,7 +291,8 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
     }
     const real v = BT::max(m0, m1);
     if (tv) {
-      if (l == lmax) Rtop[t] = v; else Rt[t * LS + (l - 1)] = v;
+      if (l != lmax) Rt[t * LS + (l - 1)] = v;
+      else if (t == k) *Rtop = v;  // the last level is read at t = k only
     }
     rcur = tv ? v : BT::ninf();
     par ^= 1;
@@ -314,13 +315,14 @@ k_dp(DPParams P, DPPlan S) {
   constexpr bool fp32 = sizeof(real) == 4;
 
   // R table [kmax+1][LS]: R(t, l) at column l-1 for the source levels
-  // l = 1..lmax-1 (row s = 0 at -inf); the last level lmax in Rtop[t].
+  // l = 1..lmax-1 (row s = 0 at -inf); the last level lmax only at t = k, in
+  // *Rtop (nothing reads it elsewhere: it is no level's source).
   // Shared memory (RSM) or, for very large B, global memory.
   real* Rt = RSM ? reinterpret_cast<real*>(sm + S.off_R)
                  : reinterpret_cast<real*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta);
-  real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // [kmax+1]
+  real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // R(k, lmax)
   U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
-  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // [32][33]
+  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
   // the R table in the CTA's scratch
@@ -386,20 +388,21 @@ k_dp(DPParams P, DPPlan S) {
       for (int j = tid; j <= k; j += T) P.trace.d_sc_ends[trace_task * P.trace.sc_stride + j] = rec[6 + j];
     __syncthreads();
     // R(t, l) for 1 <= l <= lmax
-    auto Rget = [&](int t, int l) -> real { return l == lmax ? Rtop[t] : Rt[t * LS + (l - 1)]; };
+    auto Rget = [&](int t, int l) -> real { return l == lmax ? *Rtop : Rt[t * LS + (l - 1)]; };  // l = lmax: t = k
 
     if (k >= 2) {
       for (int i = tid; i < ks * LS; i += T) Rt[i] = NINF;
-      for (int i = tid; i < ks; i += T) Rtop[i] = NINF;
+      if (tid == 0) *Rtop = NINF;
       for (int i = tid; i < 2 * 32 * LX; i += T) Xb[i] = NINF_BITS;
       __syncthreads();
       for (int t = 1 + tid; t <= k; t += T) {
         const real r1 = -entropy_term<real>(Lt, sd, SW, yhat, 0, t);
-        if (lmax == 1) Rtop[t] = r1; else Rt[t * LS] = r1;
+        if (lmax > 1) Rt[t * LS] = r1;
+        else if (t == k) *Rtop = r1;
       }
       for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block 0
         const int i = idx >> 5, j = idx & 31;
-        if (i < j && 1 + j <= k) Eb[i * 33 + j] = entropy_term<real>(Lt, sd, SW, yhat, 1 + i, 1 + j);
+        if (i < j && 1 + j <= k) Eb[j * (j - 1) / 2 + i] = entropy_term<real>(Lt, sd, SW, yhat, 1 + i, 1 + j);
       }
       if (tid == 0) s_next = 0;
       __syncthreads();
@@ -433,7 +436,7 @@ k_dp(DPParams P, DPPlan S) {
               for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block b+1
                 const int i = idx >> 5, j = idx & 31;
                 if (i < j && t1 + j <= k)
-                  Eb[i * 33 + j] = entropy_term<real>(Lt, sd, SW, yhat, t1 + i, t1 + j);
+                  Eb[j * (j - 1) / 2 + i] = entropy_term<real>(Lt, sd, SW, yhat, t1 + i, t1 + j);
               }
           }
           __syncthreads();
@@ -577,7 +580,7 @@ k_dp(DPParams P, DPPlan S) {
             wv = BT::max(wv, Rt[s * LS + (l - 1)]);
             Rt[s * LS + (l - 1)] = wv;
           }
-          Rtop[s] = BT::max(wv, Rtop[s]);
+          if (s == k) *Rtop = BT::max(wv, *Rtop);
         }
         __syncthreads();
         for (int l = 2 + warp; l <= lmax; l += NW) {
