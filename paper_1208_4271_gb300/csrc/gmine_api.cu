@@ -404,6 +404,7 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
         bool rsm = false;
         const DPPlan S = make_dp_plan((int)n, tg, fp32, th, dev.smem_optin, &rsm);
         if (S.total > dev.smem_optin) continue;
+        if (th > dp_max_threads(fp32, rsm, g.lev)) continue;  // the instance's launch bound
         int blocks = 0;
         rc = dp_occupancy(fp32, rsm, g.lev, std::max(S.total, 1), th, &blocks);
         if (rc != GMINE_OK) return rc;

@@ -26,4 +26,9 @@ cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int s
              : dp_f64_global_launch(lev, grid, threads, smem, st, P, S);
 }
 
+int dp_max_threads(bool fp32, bool rsm, int lev) {
+  if (fp32) return rsm ? dp_f32_smem_max_threads(lev) : dp_f32_global_max_threads(lev);
+  return rsm ? dp_f64_smem_max_threads(lev) : dp_f64_global_max_threads(lev);
+}
+
 }  // namespace gm

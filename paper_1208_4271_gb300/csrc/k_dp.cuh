@@ -299,8 +299,13 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
   }
 }
 
+// Launch bounds: FP32 instances with at most 20 levels per pass run as
+// 128-thread CTAs, five per SM (at most 102 registers: their shared-memory
+// plans are small, so more tasks in flight pay more than registers); the
+// others as 128- or 256-thread CTAs, two 256-thread ones per SM.
 template <typename real, bool RSM, int LEV>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(sizeof(real) == 4 && LEV <= 20 ? 128 : 256,
+                                  sizeof(real) == 4 ? (LEV <= 20 ? 5 : 2) : 1)
 k_dp(DPParams P, DPPlan S) {
   using BT = Bits<real>;
   using U = typename BT::U;
@@ -684,6 +689,10 @@ typedef void (*dp_kernel_t)(DPParams, DPPlan);
                             const DPParams& P, const DPPlan& S) {                        \
     NAME##_pick(lev)<<<grid, threads, smem, st>>>(P, S);                                 \
     return cudaGetLastError();                                                           \
+  }                                                                                      \
+  int NAME##_max_threads(int lev) {                                                      \
+    cudaFuncAttributes a;                                                                \
+    return cudaFuncGetAttributes(&a, NAME##_pick(lev)) == cudaSuccess ? a.maxThreadsPerBlock : 0; \
   }
 
 }  // namespace gm
