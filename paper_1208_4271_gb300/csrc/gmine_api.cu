@@ -194,6 +194,29 @@ SmallPlan make_small_plan(int n, const TaskBounds& tb, bool fp32, int warps) {
   return S;
 }
 
+// Shared-memory layout of the warp-per-task blocked DP kernel (float path)
+// for the tasks bounded by tb, lev levels per row of the R table.
+WarpPlan make_warp_plan(int n, const TaskBounds& tb, int lev, int warps) {
+  WarpPlan S{};
+  S.LS = lev;
+  S.xmax = std::max(tb.xmax, 2);
+  int64_t o = 0;
+  auto add = [&](int64_t b) { const int64_t at = o; o = (o + b + 15) & ~int64_t(15); return (int)at; };
+  S.off_L = add((int64_t)(n + 1) * 4);
+  S.off_warps = (int)o;
+  o = 0;
+  S.off_R = add((int64_t)(tb.kmax + 1) * S.LS * 4);
+  S.off_sd = add(4LL * tb.sd_max);
+  S.off_rbuf = add(4LL * 64);
+  S.off_Rtop = add(16);
+  S.off_lst = add(4LL * (S.xmax + 1));
+  S.off_I = add(8LL * (S.xmax + 1));
+  S.off_cuts = add(4LL * 8 * S.xmax);
+  S.warp_smem = (int)o;
+  S.total = (int)std::min<int64_t>(S.off_warps + (int64_t)warps * o, 1LL << 30);
+  return S;
+}
+
 // Shared-memory layout of the level-major DP kernel for the tasks bounded by tb.
 MidPlan make_mid_plan(int n, const TaskBounds& tb, bool fp32, int threads) {
   const int rs = fp32 ? 4 : 8;
@@ -227,7 +250,10 @@ struct DPGroup {
   bool small;      // warp-per-task kernel
   bool mid;        // level-major kernel
   bool two;        // two-column kernel (x = 2)
+  bool warp;       // warp-per-task blocked kernel (float path)
+  int tdw;         // its register row width
   int smem_two, off_two_rec, two_rec_bytes;
+  WarpPlan WS;
   DPPlan S;
   SmallPlan SS;
   MidPlan MS;
@@ -368,6 +394,30 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       g.two = false;
       g.lev = dp_level_group(fp32, 1);
     }
+    if (fp32 && g.yhi <= 15 && dp_warp_supported(g.lev, 16)) {
+      // a moderate number of levels (float path): one warp per task, the
+      // CTA size that keeps the most warps resident
+      const int tdw = ((g.yhi + 1 + 3) & ~3) <= 8 ? 8 : 16;
+      int best = 0;
+      for (int w : {4, 2, 1}) {
+        const WarpPlan wp = make_warp_plan((int)n, tg, g.lev, w);
+        if (wp.total + 1024 > dev.smem_optin) continue;
+        int blocks = 0;
+        const cudaError_t e = dp_warp_configure(g.lev, tdw, wp.total, 32 * w, &blocks, true);
+        if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+        if (blocks * w > best) {
+          best = blocks * w;
+          g.warp = true;
+          g.tdw = tdw;
+          g.WS = wp;
+          g.threads = 32 * w;
+        }
+      }
+      if (g.warp) {
+        g.scratch_per_cta = 0;
+        continue;
+      }
+    }
     if (g.lev >= 8 && g.lev <= 12) {
       // few levels, entropy triangle small enough for two CTAs per SM:
       // level-major kernel (no chain along t)
@@ -439,6 +489,22 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       int blocks = 0;
       cudaError_t e = dp_mid_configure(fp32, mmax, g.threads, &blocks, true);
       if (e == cudaSuccess) e = dp_mid_configure(fp32, g.MS.total, g.threads, &blocks, false);
+      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+      if (blocks < 1) return GMINE_E_LIMIT;
+      g.ctas = blocks * dev.sms;
+    }
+    for (int gi = 0; gi < L->ngroups; ++gi) {
+      // one attribute per warp-kernel instance (the largest plan of its
+      // groups), then each group's occupancy at its own size
+      DPGroup& g = L->grp[gi];
+      if (!g.warp) continue;
+      int wmax = 0;
+      for (int gj = 0; gj < L->ngroups; ++gj)
+        if (L->grp[gj].warp && L->grp[gj].lev == g.lev && L->grp[gj].tdw == g.tdw)
+          wmax = std::max(wmax, L->grp[gj].WS.total);
+      int blocks = 0;
+      cudaError_t e = dp_warp_configure(g.lev, g.tdw, wmax, g.threads, &blocks, true);
+      if (e == cudaSuccess) e = dp_warp_configure(g.lev, g.tdw, g.WS.total, g.threads, &blocks, false);
       if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
       if (blocks < 1) return GMINE_E_LIMIT;
       g.ctas = blocks * dev.sms;
@@ -795,6 +861,8 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
         if (g.two)
           GM_CUDA(dp_two_launch(fp32, g.ctas, g.threads, g.smem_two, st, P, g.off_two_rec,
                                 g.two_rec_bytes));
+        else if (g.warp)
+          GM_CUDA(dp_warp_launch(g.lev, g.tdw, g.ctas, g.threads, g.WS.total, st, P, g.WS));
         else if (g.mid)
           GM_CUDA(dp_mid_launch(fp32, g.ctas, g.threads, g.MS.total, st, P, g.MS));
         else if (g.small)

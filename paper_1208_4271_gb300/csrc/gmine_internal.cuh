@@ -259,6 +259,17 @@ struct SmallPlan {
   int total;
 };
 
+// Shared-memory layout of the warp-per-task blocked DP kernel (byte
+// offsets): the CTA's entropy table, then one region per warp.
+struct WarpPlan {
+  int off_L, off_warps, warp_smem;
+  int off_R, off_sd, off_rbuf, off_Rtop, off_lst, off_I, off_cuts;  // within a warp region
+  int LS;     // row stride of the R table (the level group: every level a
+              // lane's running maxima read lies inside the row)
+  int xmax;   // largest x of the launch
+  int total;
+};
+
 // Shared-memory layout of the level-major DP kernel (byte offsets).
 struct MidPlan {
   int off_E, off_R, off_L, off_rec, off_I, off_cuts, off_ecol;

@@ -57,6 +57,12 @@ GM_DP_DECLARE(dp_f64_global)
 cudaError_t dp_two_configure(bool fp32, int smem, int threads, int* blocks_per_sm);
 cudaError_t dp_two_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
                           const DPParams& P, int off_rec, int rec_bytes);
+// warp-per-task blocked DP (float path): lev levels in registers, tdw ints
+// of the lane's superclump row in registers (8: yhat <= 7, 16: yhat <= 15)
+bool dp_warp_supported(int lev, int tdw);
+cudaError_t dp_warp_configure(int lev, int tdw, int smem, int threads, int* blocks_per_sm, bool set_attr);
+cudaError_t dp_warp_launch(int lev, int tdw, int grid, int threads, int smem, cudaStream_t st,
+                           const DPParams& P, const WarpPlan& S);
 cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_sm, bool set_attr);
 cudaError_t dp_mid_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
                           const DPParams& P, const MidPlan& S);
