@@ -110,10 +110,27 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 }
 __device__ __forceinline__ double fmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
+// (r0 - e, r1 - e) for two floats packed in 64 bits (r0 in the low half)
+// in one instruction (sub.f32x2 of sm_100 and later); each element rounds
+// as the scalar subtraction does
+__device__ __forceinline__ float2 sub_x2(unsigned long long r, unsigned long long ee) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(r), "l"(ee));
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(d));
+  return v;
+}
+__device__ __forceinline__ unsigned long long splat_x2(float e) {
+  unsigned long long v;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(e));
+  return v;
+}
+
 // Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels
 // l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.  Two s
-// per iteration: each level takes both candidates in one three-operand max,
-// and the E pair of the next iteration is formed meanwhile.
+// per iteration: each level takes both candidates in one three-operand max
+// (in float two levels share one packed subtraction), and the E pair of the
+// next iteration is formed meanwhile.
 template <typename real, int LEV, bool REG>
 __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
                                            int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
@@ -135,15 +152,23 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
       const real n1 = more ? E(s + 3) : e1;
       const real* R0 = Rt + s * LS + (lc - 2);
       const real* R1 = R0 + LS;
+      unsigned long long ee0 = 0, ee1 = 0;
+      if constexpr (sizeof(real) == 4) {
+        ee0 = splat_x2(e0);
+        ee1 = splat_x2(e1);
+      }
 #pragma unroll
       for (int g = 0; g < LEV / VW; ++g) {
         if constexpr (sizeof(real) == 4) {
-          const float4 a = *reinterpret_cast<const float4*>(R0 + 4 * g);
-          const float4 b = *reinterpret_cast<const float4*>(R1 + 4 * g);
-          acc[4 * g + 0] = fmax3(acc[4 * g + 0], a.x - e0, b.x - e1);
-          acc[4 * g + 1] = fmax3(acc[4 * g + 1], a.y - e0, b.y - e1);
-          acc[4 * g + 2] = fmax3(acc[4 * g + 2], a.z - e0, b.z - e1);
-          acc[4 * g + 3] = fmax3(acc[4 * g + 3], a.w - e0, b.w - e1);
+          // four levels of rows s and s+1, two subtractions per instruction
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(R0 + 4 * g);
+          const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(R1 + 4 * g);
+          const float2 a0 = sub_x2(a.x, ee0), a1 = sub_x2(a.y, ee0);
+          const float2 b0 = sub_x2(b.x, ee1), b1 = sub_x2(b.y, ee1);
+          acc[4 * g + 0] = fmax3(acc[4 * g + 0], a0.x, b0.x);
+          acc[4 * g + 1] = fmax3(acc[4 * g + 1], a0.y, b0.y);
+          acc[4 * g + 2] = fmax3(acc[4 * g + 2], a1.x, b1.x);
+          acc[4 * g + 3] = fmax3(acc[4 * g + 3], a1.y, b1.y);
         } else {
           const double2 a = *reinterpret_cast<const double2*>(R0 + 2 * g);
           const double2 b = *reinterpret_cast<const double2*>(R1 + 2 * g);
@@ -243,6 +268,34 @@ __host__ __device__ __forceinline__ int level_group(int nlev) {
   return 40;
 }
 
+// Named barrier 1 (barrier 0 is __syncthreads): warp 0 arrives once it has
+// read the in-block triangle, the other warps wait there before they
+// overwrite it; nthreads = the CTA's threads, all of them take part.
+__device__ __forceinline__ void bar_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void bar_wait(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Entries of the in-block entropy triangle of the block starting at t0:
+// E(t0+i, t0+j), 0 <= i < j <= 31, at j(j-1)/2 + i (those with t0+j <= k),
+// entry p by thread u, u + U, ...
+constexpr int kEbEntries = 32 * 31 / 2;
+template <typename real>
+__device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const real* __restrict__ Lt,
+                                                   const int* __restrict__ sd, int SW, int yhat, int t0,
+                                                   int k, int u, int U) {
+  int j = 1, base = 0;  // base = j(j-1)/2
+  for (int p = u; p < kEbEntries; p += U) {
+    while (base + j <= p) {
+      base += j;
+      ++j;
+    }
+    if (t0 + j <= k) Eb[p] = entropy_term<real>(Lt, sd, SW, yhat, t0 + (p - base), t0 + j);
+  }
+}
+
 // The candidates of block b with s inside the block, level after level:
 // lane j owns t0+j and keeps the column E(t0+i, t0+j), i < j, in registers
 // (+inf for i >= j, so those candidates are -inf).  At level l the 32
@@ -256,7 +309,7 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
                                               int LX, int lmax, int t0, int k,
                                               const typename Bits<real>::U* __restrict__ Xcur,
                                               bool has_x, const real* __restrict__ Eb,
-                                              real* __restrict__ rbuf, int lane) {
+                                              real* __restrict__ rbuf, int lane, int release_T) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   const int t = t0 + lane;
@@ -267,6 +320,11 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
   real ec[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) ec[i] = (tv && i < lane) ? Eb[lane * (lane - 1) / 2 + i] : pinf;
+  if (release_T > 0) {
+    // the triangle is in registers: the other warps may overwrite it
+    __syncwarp();
+    bar_arrive(1, release_T);
+  }
   real rcur = tv ? Rt[t * LS] : BT::ninf();  // level 1
   const typename Bits<real>::U* xr = Xcur + lane * LX;
   int par = 0;
@@ -327,7 +385,7 @@ k_dp(DPParams P, DPPlan S) {
                  : reinterpret_cast<real*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta);
   real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // R(k, lmax)
   U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
-  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);      // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
+  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);  // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
   // the R table in the CTA's scratch
@@ -405,10 +463,7 @@ k_dp(DPParams P, DPPlan S) {
         if (lmax > 1) Rt[t * LS] = r1;
         else if (t == k) *Rtop = r1;
       }
-      for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block 0
-        const int i = idx >> 5, j = idx & 31;
-        if (i < j && 1 + j <= k) Eb[j * (j - 1) / 2 + i] = entropy_term<real>(Lt, sd, SW, yhat, 1 + i, 1 + j);
-      }
+      in_block_entropies<real>(Eb, Lt, sd, SW, yhat, 1, k, tid, T);  // block 0
       if (tid == 0) s_next = 0;
       __syncthreads();
 
@@ -422,9 +477,17 @@ k_dp(DPParams P, DPPlan S) {
         const int tn = t1 + lane;  // this lane's t in block b+1
         const bool tnv = next && tn <= k;
         const int ttn = tnv ? tn : k;
+        // block b+1's in-block triangle replaces block b's while warp 0
+        // solves block b (every thread takes the same branch: next, NW)
+        const bool eb_early = next && NW > 1;
         for (int step = 0; step < 2; ++step) {
           if (step == 0 && warp == 0)  // ---- block b, s inside the block
-            phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, Eb, rbuf, lane);
+            phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, Eb, rbuf, lane,
+                                eb_early ? T : 0);
+          if (step == 0 && eb_early && warp > 0) {
+            bar_wait(1, T);
+            in_block_entropies<real>(Eb, Lt, sd, SW, yhat, t1, k, tid - 32, T - 32);
+          }
           // step 0: A1 of block b+1, s in [1, t0 - 1], shared work counter
           // (warp 0 joins once block b is solved);
           // step 1: A2 of block b+1, s in block b, static split
@@ -437,12 +500,7 @@ k_dp(DPParams P, DPPlan S) {
           if (step == 1) {
             for (int i = tid; i < 32 * LX; i += T) Xcur[i] = NINF_BITS;  // for block b+2
             if (tid == 0) s_next = 0;
-            if (next)
-              for (int idx = tid; idx < 32 * 32; idx += T) {  // within-block entropies of block b+1
-                const int i = idx >> 5, j = idx & 31;
-                if (i < j && t1 + j <= k)
-                  Eb[j * (j - 1) / 2 + i] = entropy_term<real>(Lt, sd, SW, yhat, t1 + i, t1 + j);
-              }
+            if (next && NW == 1) in_block_entropies<real>(Eb, Lt, sd, SW, yhat, t1, k, tid, T);
           }
           __syncthreads();
         }

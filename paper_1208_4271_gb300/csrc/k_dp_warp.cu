@@ -8,7 +8,8 @@
 // of 32, lane j owning t = t0 + j, and one warp takes a block in two steps:
 //   A: every s below the block: E(s,t) once per (s, t), then the running
 //      maxima of all LEV levels in registers (the R row of s is a warp-wide
-//      16-byte broadcast), two s per three-operand max;
+//      16-byte broadcast), two subtractions per packed instruction and two
+//      s per three-operand max;
 //   B: s inside the block, level after level: lane j keeps E(t0+i, t0+j),
 //      i < j, in registers and reads the 32 values R(t0+i, l-1) of the level
 //      below as eight 16-byte broadcasts.
@@ -162,14 +163,17 @@ __global__ void __launch_bounds__(128, 4) k_dp_warp(DPParams P, WarpPlan S) {
             const float n1 = more ? entropy_w<TDW>(Lt, sd, SW, yhat, td, s + 3) : e1;
             const float* R0 = Rt + s * LS;
             const float* R1 = R0 + LS;
+            const unsigned long long ee0 = splat_x2(e0), ee1 = splat_x2(e1);
 #pragma unroll
             for (int g = 0; g < LEV / 4; ++g) {
-              const float4 a = *reinterpret_cast<const float4*>(R0 + 4 * g);
-              const float4 c = *reinterpret_cast<const float4*>(R1 + 4 * g);
-              acc[4 * g + 0] = fmax3(acc[4 * g + 0], a.x - e0, c.x - e1);
-              acc[4 * g + 1] = fmax3(acc[4 * g + 1], a.y - e0, c.y - e1);
-              acc[4 * g + 2] = fmax3(acc[4 * g + 2], a.z - e0, c.z - e1);
-              acc[4 * g + 3] = fmax3(acc[4 * g + 3], a.w - e0, c.w - e1);
+              const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(R0 + 4 * g);
+              const ulonglong2 c = *reinterpret_cast<const ulonglong2*>(R1 + 4 * g);
+              const float2 a0 = sub_x2(a.x, ee0), a1 = sub_x2(a.y, ee0);
+              const float2 c0 = sub_x2(c.x, ee1), c1 = sub_x2(c.y, ee1);
+              acc[4 * g + 0] = fmax3(acc[4 * g + 0], a0.x, c0.x);
+              acc[4 * g + 1] = fmax3(acc[4 * g + 1], a0.y, c0.y);
+              acc[4 * g + 2] = fmax3(acc[4 * g + 2], a1.x, c1.x);
+              acc[4 * g + 3] = fmax3(acc[4 * g + 3], a1.y, c1.y);
             }
             e0 = n0;
             e1 = n1;
