@@ -315,6 +315,31 @@ def main():
                           % (Ps.shape[0], sub)}
         del ws64
 
+    # Pearson rho and the non-linearity index MIC - rho^2 of every pair of
+    # the step, from the timed step's scores (inputs resident; L2 flushed
+    # before each of three timed launches)
+    rho_d = torch.empty(max(npairs, 1), dtype=torch.float64, device=dev)
+    nl_d = torch.empty(max(npairs, 1), dtype=torch.float64, device=dev)
+
+    def step_lin():
+        rc = gmine.lib().gmine_pearson_batch(
+            gmine._dptr(Vd), p, n, gmine._dptr(Pd), npairs, gmine._dptr(scores),
+            gmine._dptr(rho_d), gmine._dptr(nl_d), gmine._stream_ptr(stream))
+        gmine._check(rc, "gmine_pearson_batch")
+    step_lin()
+    torch.cuda.synchronize(dev)
+    lin_ms = 0.0
+    for _ in range(3):
+        flush.zero_()
+        e0.record(stream)
+        step_lin()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        lin_ms += e0.elapsed_time(e1) / 3
+    linear = {"value": world * npairs / (lin_ms / 1e3), "unit": "pairs/s", "ms": lin_ms,
+              "what": "Pearson rho and MIC - rho^2 of every pair (gmine_pearson_batch, FP64), "
+                      "one launch, mean of 3"}
+
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -362,6 +387,17 @@ def main():
                                                      ref64["stats"])
             parity["fp64_sample_pairs"] = int(i64.size)
         parity["partition_flips_fp32"] = partition_flips(Vd, dev, min(40, p))
+        # Pearson rho of the oracle's sample of pairs
+        import oracle
+        rho_h = rho_d.cpu().numpy()
+        rerr = 0.0
+        for i in keep["idx"][:2000]:
+            r_ref, _ = oracle.pearson(V[P[i, 0]], V[P[i, 1]])
+            if np.isnan(r_ref) != np.isnan(rho_h[i]):
+                rerr = float("inf")
+            elif not np.isnan(r_ref):
+                rerr = max(rerr, abs(float(rho_h[i]) - r_ref))
+        parity["rho_vs_oracle"] = {"max": rerr, "pairs": int(min(2000, keep["idx"].size))}
 
     if rank != 0:
         return
@@ -383,9 +419,10 @@ def main():
                        "pairs_per_gpu": npairs, "dp": "fp32 with int32 counts, fp64 re-score",
                        "l2": "256 MiB buffer written between timed steps"},
             "plain_fp64": fp64,
+            "linear": linear,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcand/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_mid, k_dp_small, k_dp_two)",
+                         "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_warp, k_dp_mid, k_dp_small, k_dp_two)",
                          "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr per DP step"
                                        % (sms, fmax),
                          "dp_candidates_per_step": cand // max(args.steps, 1),

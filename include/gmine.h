@@ -216,6 +216,29 @@ int gmine_compute_batch_static(const double *d_vars, int64_t p, int64_t n,
                                gmine_pair_score *d_scores, double *d_M,
                                void *stream);
 
+/* ---- the linear statistics reported beside MINE ------------------------ */
+
+/* Pearson correlation and the non-linearity index of each listed pair: the
+   paper's analyses report them next to the four MINE statistics (Fig. 1
+   caption; SI Sec. 2A, "four MINE statistics, Pearson and non-linearity").
+   - d_rho[i]: Pearson rho of pair i over the samples where both variables
+     are finite (the same samples as its MINE score), the two-pass form
+     S_xy / sqrt(S_xx * S_yy) in double; NaN when fewer than two samples
+     remain, a variance is zero or a pair index is outside [0, p).
+   - d_nonlin[i] (may be NULL): MIC - rho^2, the paper naming the index
+     without a formula and this being its definition in the MINE statistics'
+     original paper; needs d_scores from gmine_compute_batch* for the same
+     pairs (NULL d_scores with non-NULL d_nonlin is GMINE_E_ARG).  NaN where
+     rho is NaN or the pair's status is not GMINE_OK.
+   Layouts as for gmine_compute_batch (d_vars [p][n], d_pairs [n_pairs][2]);
+   all pointers are device pointers owned by the caller; asynchronous on
+   `stream`; nothing is allocated.  Errors: GMINE_E_ARG for negative sizes or
+   missing pointers, GMINE_E_CUDA if the launch fails. */
+int gmine_pearson_batch(const double *d_vars, int64_t p, int64_t n,
+                        const int32_t *d_pairs, int64_t n_pairs,
+                        const gmine_pair_score *d_scores, double *d_rho,
+                        double *d_nonlin, void *stream);
+
 /* ---- single steps, the same kernels as the batch uses ------------------ */
 
 /* Tie-aware sort of every variable (finite samples; no NaN allowed):

@@ -56,6 +56,8 @@ def lib():
                                          ctypes.c_double, _dp, _ip, _ip, _dp,
                                          _lp, ctypes.c_int]
         L.oracle_score_batch.restype = ctypes.c_int
+        L.oracle_pearson.argtypes = [_dp, _dp, ctypes.c_int, _ip]
+        L.oracle_pearson.restype = ctypes.c_double
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -203,6 +205,22 @@ def score_batch(vars_, pairs, alpha=0.6, c=15.0, nthreads=0, want_M=False):
         out["M"] = M
         out["M_offsets"] = offs
     return out
+
+
+def pearson(x, y):
+    """Pearson rho over the samples where x and y are both finite (Fig. 1;
+    reading R11): returns (rho, n_used); rho is NaN when fewer than two
+    samples remain or a variance is zero."""
+    x, y = _d(x), _d(y)
+    assert len(x) == len(y)
+    m = np.zeros(1, dtype=np.int32)
+    r = lib().oracle_pearson(_pd(x), _pd(y), len(x), _pi(m))
+    return float(r), int(m[0])
+
+
+def nonlinearity(mic, rho):
+    """The non-linearity index MIC - rho^2 (reading R11)."""
+    return float(mic) - float(rho) * float(rho)
 
 
 def max_threads():

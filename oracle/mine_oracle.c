@@ -38,6 +38,11 @@
  *      (Appendix item 4); min(l, yhat) < 2 gives 0.
  *   R9 MCN uses log2 and epsilon = 0 over x*y <= B (Appendix item 2).
  *   R10 a sample whose x or y is not finite is dropped from that pair.
+ *   R11 Pearson rho (reported beside the MINE statistics, Fig. 1) is the
+ *      two-pass textbook form over the pair's finite samples, NaN when fewer
+ *      than two remain or a variance is zero; the non-linearity index the
+ *      paper names without a formula is MIC - rho^2 (the MINE statistics'
+ *      original definition), for pairs whose score is valid.
  */
 #include <math.h>
 #include <stdint.h>
@@ -568,6 +573,43 @@ int oracle_score_batch(const double *vars, int p, int n, const int *pairs,
     free(Mbuf);
 #endif
     return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pearson correlation, the linear statistic the paper reports beside the    */
+/* four MINE statistics (Fig. 1 caption; SI Sec. 2A: "four MINE statistics,  */
+/* Pearson and non-linearity"), over the samples where x and y are both      */
+/* finite (reading R10).  The textbook two-pass definition: means first,     */
+/*   rho = S_xy / sqrt(S_xx * S_yy),  S_ab = sum_i (a_i - mean a)(b_i - mean b) */
+/* with every sum in increasing i.  NaN when fewer than two samples remain   */
+/* or a variance is zero (reading R11).  *n_used gets the sample count.      */
+/* ------------------------------------------------------------------------ */
+
+double oracle_pearson(const double *x, const double *y, int n, int *n_used)
+{
+    int m = 0;
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < n; i++) {
+        if (isfinite(x[i]) && isfinite(y[i])) {
+            sx += x[i];
+            sy += y[i];
+            m++;
+        }
+    }
+    if (n_used) *n_used = m;
+    if (m < 2) return NAN;
+    const double mx = sx / (double)m, my = sy / (double)m;
+    double sxy = 0.0, sxx = 0.0, syy = 0.0;
+    for (int i = 0; i < n; i++) {
+        if (isfinite(x[i]) && isfinite(y[i])) {
+            const double dx = x[i] - mx, dy = y[i] - my;
+            sxy += dx * dy;
+            sxx += dx * dx;
+            syy += dy * dy;
+        }
+    }
+    if (!(sxx > 0.0) || !(syy > 0.0)) return NAN;
+    return sxy / sqrt(sxx * syy);
 }
 
 /* Threads OpenMP would use (1 without OpenMP). */

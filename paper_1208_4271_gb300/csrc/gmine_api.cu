@@ -985,6 +985,23 @@ int gmine_equipartition(const double* d_vars, int64_t p, int64_t n, int32_t y, i
   return GMINE_OK;
 }
 
+int gmine_pearson_batch(const double* d_vars, int64_t p, int64_t n, const int32_t* d_pairs,
+                        int64_t n_pairs, const gmine_pair_score* d_scores, double* d_rho,
+                        double* d_nonlin, void* stream) {
+  if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
+  if (n_pairs == 0) return GMINE_OK;
+  if (!plausible_device_ptr(d_vars) || !d_pairs || !d_rho) return GMINE_E_ARG;
+  if (d_nonlin && !d_scores) return GMINE_E_ARG;
+  DeviceInfo dev;
+  const int rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  // eight 256-thread CTAs (64 warps, one pair each) per SM, grid-stride
+  const int64_t grid = std::min<int64_t>((n_pairs + 7) / 8, (int64_t)dev.sms * 8);
+  GM_CUDA(pearson_launch((int)grid, static_cast<cudaStream_t>(stream), d_vars, p, n, d_pairs,
+                         n_pairs, d_scores, d_rho, d_nonlin));
+  return GMINE_OK;
+}
+
 int gmine_score_pair_host(const double* h_x, const double* h_y, int64_t n,
                           const gmine_param* param, int32_t precision, gmine_pair_score* out,
                           double* M_out) {

@@ -67,6 +67,11 @@ cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_s
 cudaError_t dp_mid_launch(bool fp32, int grid, int threads, int smem, cudaStream_t st,
                           const DPParams& P, const MidPlan& S);
 
+// Pearson rho and the non-linearity index per pair (k_pearson.cu)
+cudaError_t pearson_launch(int grid, cudaStream_t st, const double* d_vars, int64_t p, int64_t n,
+                           const int32_t* d_pairs, int64_t n_pairs, const gmine_pair_score* d_scores,
+                           double* d_rho, double* d_nonlin);
+
 // Records a CUDA error for gmine_strerror (host code outside gmine_api.cu).
 void note_cuda_error(cudaError_t e);
 

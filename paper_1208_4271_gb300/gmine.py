@@ -79,6 +79,7 @@ def lib():
         L.gmine_rank.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp]
         L.gmine_equipartition.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64, _vp]
         L.gmine_score_pair_host.argtypes = [_vp, _vp, _i64, ctypes.POINTER(Param), _i32, _vp, _vp]
+        L.gmine_pearson_batch.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _vp]
         for f in ("gmine_mic", "gmine_mas", "gmine_mev", "gmine_mcn"):
             getattr(L, f).argtypes = [_vp]
             getattr(L, f).restype = ctypes.c_double
@@ -255,6 +256,27 @@ def compute_batch_static(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, 
                                           ctypes.byref(Param(alpha, c)), int(precision),
                                           _dptr(scores), _dptr(M), _stream_ptr(stream))
     return rc, scores[:n_pairs], M
+
+
+def pearson_batch(vars_, pairs, scores=None, stream=None):
+    """gmine_pearson_batch: Pearson rho of each pair over its finite samples
+    and, when `scores` (from compute_batch on the same pairs) is given, the
+    non-linearity index MIC - rho^2.  Returns (rho, nonlin or None), CUDA
+    float64 [n_pairs] tensors; asynchronous on the stream."""
+    import torch
+    assert vars_.is_cuda and vars_.dtype == torch.float64 and vars_.is_contiguous()
+    assert pairs.is_cuda and pairs.dtype == torch.int32 and pairs.is_contiguous()
+    p, n = vars_.shape
+    n_pairs = pairs.shape[0]
+    rho = torch.empty(max(n_pairs, 1), dtype=torch.float64, device=vars_.device)
+    nonlin = None
+    if scores is not None:
+        assert scores.is_cuda and scores.shape[0] == n_pairs and scores.is_contiguous()
+        nonlin = torch.empty(max(n_pairs, 1), dtype=torch.float64, device=vars_.device)
+    _check(lib().gmine_pearson_batch(_dptr(vars_), p, n, _dptr(pairs), n_pairs, _dptr(scores),
+                                     _dptr(rho), _dptr(nonlin), _stream_ptr(stream)),
+           "gmine_pearson_batch")
+    return rho[:n_pairs], (nonlin[:n_pairs] if nonlin is not None else None)
 
 
 def scores_to_numpy(scores):

@@ -68,3 +68,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(gmine, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError):
         gmine.lib()
+
+
+def test_pearson_batch_argument_checks(lib):
+    vp = ctypes.c_void_p
+    dummy = vp(16)  # never dereferenced: every call below fails its checks first
+    assert lib.gmine_pearson_batch(None, 2, 10, dummy, 1, None, dummy, None, None) == gmine.E_ARG
+    assert lib.gmine_pearson_batch(dummy, 2, 10, None, 1, None, dummy, None, None) == gmine.E_ARG
+    assert lib.gmine_pearson_batch(dummy, 2, 10, dummy, 1, None, None, None, None) == gmine.E_ARG
+    # the non-linearity index needs the scores of the same pairs
+    assert lib.gmine_pearson_batch(dummy, 2, 10, dummy, 1, None, dummy, dummy, None) == gmine.E_ARG
+    assert lib.gmine_pearson_batch(dummy, -1, 10, dummy, 1, None, dummy, None, None) == gmine.E_ARG
+    # nothing to do is success without touching a device
+    assert lib.gmine_pearson_batch(None, 0, 0, None, 0, None, None, None, None) == gmine.OK

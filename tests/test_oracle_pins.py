@@ -10,7 +10,10 @@
   against exhaustive search over every grid;
 * invariants: MIC = 1 for noiseless functional pairs, 0 <= M <= 1, bitwise
   invariance under order-preserving transforms and sample permutations,
-  transposition of M when x and y swap.
+  transposition of M when x and y swap;
+* Pearson rho: a hand-computed example, exact linear relations, symmetry and
+  affine invariance, numpy's corrcoef, missing samples; the non-linearity
+  index on a symmetric parabola and a line.
 
 Mutual information in the brute-force checks is the textbook
 sum_jr p_jr ln(p_jr / (p_j p_r)), not the oracle's H(Q) - sum E / n form.
@@ -491,3 +494,73 @@ def test_dp_empty_column_candidate_is_kept():
     for j in range(len(bounds) - 1):
         cols[bounds[j]:bounds[j + 1]] = j
     assert abs(textbook_mi(cols, qs) - res["I"][5 - 2]) <= 1e-12
+
+
+# ---- Pearson rho (reported beside the MINE statistics, Fig. 1; reading R11)
+
+def test_pearson_hand_example():
+    # x = 1..5, y = (2, 4, 5, 4, 5): means 3 and 4, S_xy = 6, S_xx = 10,
+    # S_yy = 6, so rho = 6 / sqrt(60) = sqrt(0.6)
+    r, m = oracle.pearson([1, 2, 3, 4, 5], [2, 4, 5, 4, 5])
+    assert m == 5
+    assert abs(r - math.sqrt(0.6)) <= 2e-16
+
+
+def test_pearson_closed_forms_and_invariants():
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=400)
+    y = 0.3 * x + rng.normal(size=400)
+    r, _ = oracle.pearson(x, y)
+    # exact linear relations give +-1; rho(x, x) = 1
+    assert abs(oracle.pearson(x, 2.5 * x - 7.0)[0] - 1.0) <= 1e-14
+    assert abs(oracle.pearson(x, -0.5 * x + 1.0)[0] + 1.0) <= 1e-14
+    assert abs(oracle.pearson(x, x)[0] - 1.0) <= 1e-15
+    # symmetric; invariant under positive affine maps, sign flips with a
+    # negative scale
+    assert abs(oracle.pearson(y, x)[0] - r) <= 1e-15
+    assert abs(oracle.pearson(3.0 * x + 2.0, 0.25 * y - 9.0)[0] - r) <= 1e-13
+    assert abs(oracle.pearson(-x, y)[0] + r) <= 1e-15
+    assert -1.0 <= r <= 1.0
+
+
+def test_pearson_matches_numpy_corrcoef():
+    # an independent library routine (numpy's covariance-based corrcoef)
+    rng = np.random.default_rng(12)
+    for n in (2, 3, 10, 1340):
+        x = rng.lognormal(6.0, 1.5, size=n)
+        y = np.sin(x / 200.0) + rng.normal(scale=0.3, size=n)
+        r, _ = oracle.pearson(x, y)
+        assert abs(r - np.corrcoef(x, y)[0, 1]) <= 1e-12
+
+
+def test_pearson_missing_samples_and_degenerate_cases():
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=200)
+    y = x ** 2 + rng.normal(size=200)
+    xm, ym = x.copy(), y.copy()
+    xm[::7] = np.nan
+    ym[3::11] = np.inf
+    keep = np.isfinite(xm) & np.isfinite(ym)
+    r, m = oracle.pearson(xm, ym)
+    r2, m2 = oracle.pearson(x[keep], y[keep])
+    assert m == m2 == int(keep.sum())
+    assert r == r2  # the same samples in the same order: the same double
+    assert math.isnan(oracle.pearson([1.0], [2.0])[0])               # one sample
+    assert math.isnan(oracle.pearson([1.0, 1.0, 1.0], [1.0, 2.0, 3.0])[0])  # zero variance
+    assert math.isnan(oracle.pearson([np.nan, 1.0], [1.0, np.nan])[0])      # nothing left
+
+
+def test_nonlinearity_index():
+    # noiseless y = x^2 on a symmetric grid: rho = 0 by symmetry (up to
+    # rounding) while MIC is near 1 (a function), so the index is MIC itself
+    # and close to 1; a noiseless line has MIC = 1 and rho = 1: index 0
+    x = np.linspace(-1.0, 1.0, 201)
+    s = oracle.score_pair(x, x * x)
+    r, _ = oracle.pearson(x, x * x)
+    assert abs(r) <= 1e-13
+    idx = oracle.nonlinearity(s["mic"], r)
+    assert abs(idx - s["mic"]) <= 1e-25 and idx > 0.99
+    s = oracle.score_pair(x, 3.0 * x)
+    r, _ = oracle.pearson(x, 3.0 * x)
+    assert abs(s["mic"] - 1.0) <= 1e-15
+    assert abs(oracle.nonlinearity(s["mic"], r)) <= 1e-14
