@@ -60,6 +60,17 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of the ranks' values (a step is as slow as the slowest
+    rank); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -283,10 +294,7 @@ def main():
     barrier()
     clk = clocks.stop()
     ms_step = elapsed / args.steps
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step_max = float(t.item())
+    ms_step_max = max_over_ranks(ms_step, dist, dev)
     value = world * npairs / (ms_step_max / 1e3)
 
     # the plain FP64 DP on all pairs of the first fp64_vars variables
