@@ -88,7 +88,8 @@ typedef struct {
     int32_t B;          /* floor(n_used^alpha)                            */
     int32_t m_cells;    /* cells (x, y), x, y >= 2, x*y <= B, y-major     */
     int32_t mcn_xy;     /* the x*y whose log2 is MCN                      */
-    int32_t status;     /* GMINE_OK, GMINE_E_TOO_FEW or GMINE_E_CONSTANT  */
+    int32_t status;     /* GMINE_OK, GMINE_E_TOO_FEW, GMINE_E_CONSTANT, or
+                           GMINE_E_ARG for a pair index outside [0, p)    */
     int32_t yhat_x;     /* rows used when X is equipartitioned into 2     */
     int32_t yhat_y;     /* rows used when Y is equipartitioned into 2     */
     int32_t reserved;
