@@ -192,3 +192,38 @@ def tie_heavy(p=8, n=400, levels=6, seed_salt=0):
     V = rng.integers(0, levels, (p, n)).astype(np.float64)
     V[1::2] = V[0::2] + rng.integers(0, 2, (p // 2, n))
     return V, all_pairs(p)
+
+
+def uniform_pairs(n, reps, seed_salt=0):
+    """The scaling experiment's input (SI Sec. 2C): reps independent pairs of
+    two uniformly distributed random vectors of length n (the paper times
+    100 replicates per size).  Returns (vars [2*reps, n], pairs [reps, 2])."""
+    rng = _rng(7, 1000 * seed_salt + int(n))
+    V = rng.uniform(0.0, 1.0, (2 * reps, n))
+    pairs = np.arange(2 * reps, dtype=np.int32).reshape(-1, 2)
+    return V, pairs
+
+
+def sparse_count_pairs(n=675, n_pairs=6, seed_salt=0):
+    """Stand-in for the microbiome OTU pairs of the c-convergence figure
+    (SI Sec. 1, n = 675 samples, alpha = 0.551): sparse abundance counts with
+    many zeros (heavy ties), each pair sharing a latent factor through a
+    different relation (monotone, quadratic, threshold), so that clumps and
+    superclumps matter.  Returns (vars [2*n_pairs, n], pairs)."""
+    rng = _rng(8, seed_salt)
+    V = np.empty((2 * n_pairs, n))
+    for i in range(n_pairs):
+        f = rng.normal(0.0, 1.0, n)
+        kind = i % 3
+        if kind == 0:
+            g = f + 0.5 * rng.normal(0.0, 1.0, n)
+        elif kind == 1:
+            g = f * f - 1.0 + 0.5 * rng.normal(0.0, 1.0, n)
+        else:
+            g = np.where(f > 0.3, 1.5, -0.5) + 0.5 * rng.normal(0.0, 1.0, n)
+        for j, z in enumerate((f, g)):
+            present = rng.uniform(0.0, 1.0, n) < rng.uniform(0.3, 0.7)  # many absent taxa
+            mean = np.exp(1.5 + 0.8 * z)
+            V[2 * i + j] = np.where(present, rng.poisson(mean), 0).astype(np.float64)
+    pairs = np.arange(2 * n_pairs, dtype=np.int32).reshape(-1, 2)
+    return V, pairs
