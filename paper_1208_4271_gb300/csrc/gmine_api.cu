@@ -475,6 +475,26 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
     }
     g.scratch_per_cta = dp_scratch(tg, g.S, fp32, g.rsm);
   }
+  for (int gi = 0; gi < L->ngroups; ++gi) {
+    // an instance of the blocked kernel can serve several groups (row counts
+    // with four levels are split by x; a two-column group may fall back to
+    // it): one attribute per instance (the largest plan of its groups), then
+    // each group's occupancy at its own size
+    DPGroup& g = L->grp[gi];
+    auto blocked = [](const DPGroup& h) { return !(h.two || h.warp || h.mid || h.small); };
+    if (!blocked(g)) continue;
+    int smax = 1;
+    for (int gj = 0; gj < L->ngroups; ++gj) {
+      const DPGroup& h = L->grp[gj];
+      if (blocked(h) && h.rsm == g.rsm && h.lev == g.lev) smax = std::max(smax, h.S.total);
+    }
+    int blocks = 0;
+    cudaError_t e = dp_configure(fp32, g.rsm, g.lev, smax, g.threads, &blocks);
+    if (e == cudaSuccess) e = dp_occupancy_only(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
+    if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+    if (blocks < 1) return GMINE_E_LIMIT;
+    g.ctas = blocks * dev.sms;
+  }
   {
     // the warp-per-task kernel is shared by its groups: one attribute (the
     // largest plan), then each group's occupancy at its own size

@@ -26,6 +26,13 @@ cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int s
              : dp_f64_global_launch(lev, grid, threads, smem, st, P, S);
 }
 
+cudaError_t dp_occupancy_only(bool fp32, bool rsm, int lev, int smem, int threads, int* blocks_per_sm) {
+  if (fp32) return rsm ? dp_f32_smem_occupancy(lev, smem, threads, blocks_per_sm)
+                       : dp_f32_global_occupancy(lev, smem, threads, blocks_per_sm);
+  return rsm ? dp_f64_smem_occupancy(lev, smem, threads, blocks_per_sm)
+             : dp_f64_global_occupancy(lev, smem, threads, blocks_per_sm);
+}
+
 int dp_max_threads(bool fp32, bool rsm, int lev) {
   if (fp32) return rsm ? dp_f32_smem_max_threads(lev) : dp_f32_global_max_threads(lev);
   return rsm ? dp_f64_smem_max_threads(lev) : dp_f64_global_max_threads(lev);

@@ -748,6 +748,9 @@ typedef void (*dp_kernel_t)(DPParams, DPPlan);
     NAME##_pick(lev)<<<grid, threads, smem, st>>>(P, S);                                 \
     return cudaGetLastError();                                                           \
   }                                                                                      \
+  cudaError_t NAME##_occupancy(int lev, int smem, int threads, int* blocks_per_sm) {     \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, NAME##_pick(lev), threads, smem); \
+  }                                                                                      \
   int NAME##_max_threads(int lev) {                                                      \
     cudaFuncAttributes a;                                                                \
     return cudaFuncGetAttributes(&a, NAME##_pick(lev)) == cudaSuccess ? a.maxThreadsPerBlock : 0; \

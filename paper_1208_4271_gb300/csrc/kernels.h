@@ -41,12 +41,15 @@ cudaError_t dp_configure(bool fp32, bool rsm, int lev, int smem, int threads, in
 cudaError_t dp_launch(bool fp32, bool rsm, int lev, int grid, int threads, int smem,
                       cudaStream_t st, const DPParams& P, const DPPlan& S);
 int dp_max_threads(bool fp32, bool rsm, int lev);  // the instance's launch bound
+// blocks per SM at `smem` bytes, leaving the instance's attribute as it is
+cudaError_t dp_occupancy_only(bool fp32, bool rsm, int lev, int smem, int threads, int* blocks_per_sm);
 // one pair per instance set (k_dp_{f32,f64}_{smem,global}.cu); dp_configure
 // and dp_launch dispatch to them
 #define GM_DP_DECLARE(NAME)                                                            \
   cudaError_t NAME##_configure(int lev, int smem, int threads, int* blocks_per_sm);     \
   cudaError_t NAME##_launch(int lev, int grid, int threads, int smem, cudaStream_t st,  \
                             const DPParams& P, const DPPlan& S);                        \
+  cudaError_t NAME##_occupancy(int lev, int smem, int threads, int* blocks_per_sm);     \
   int NAME##_max_threads(int lev);
 GM_DP_DECLARE(dp_f32_smem)
 GM_DP_DECLARE(dp_f32_global)

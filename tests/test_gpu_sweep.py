@@ -19,7 +19,9 @@ def _cuda():
 
 
 def test_c_sweep_matches_oracle():
-    cs = [1.0, 2.0, 50.0]
+    # c = 120: the row counts with four levels (split by x) all take the
+    # blocked kernel's 4-level instance, with different shared-memory plans
+    cs = [1.0, 2.0, 50.0, 120.0]
     recs = sweep.c_sweep(cs, n=675, n_pairs=3, alpha=0.551)
     S, Q = workloads.sparse_count_pairs(675, 3)
     ref = {c: oracle.score_batch(S, Q, 0.551, c)["stats"][:, 0] for c in cs}
@@ -33,7 +35,7 @@ def test_c_sweep_matches_oracle():
     assert seen == 2 * len(cs)
     conv = [r for r in recs if r["sweep"] == "c_convergence"]
     assert len(conv) == 2 * len(cs)
-    assert all(r["max_abs_diff_to_c_max"] == 0.0 for r in conv if r["c"] == 50.0)
+    assert all(r["max_abs_diff_to_c_max"] == 0.0 for r in conv if r["c"] == 120.0)
 
 
 def test_time_sweep_small():
