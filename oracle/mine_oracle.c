@@ -155,51 +155,51 @@ int oracle_equipartition(const double *v, int n, int y, int *Q)
 }
 
 /* ------------------------------------------------------------------------ */
-/* GetClumpsPartition (Appendix item 5, Algorithm GetClumpsPartition,        */
-/* worked example Fig. getclumps).                                           */
+/* GetClumpsPartition (Appendix item 5; worked example Fig. getclumps).     */
 /*                                                                           */
-/* In increasing order of u, every maximal run of equal u-values (x-tie run) */
-/* whose Q labels are not all the same is given one fresh label, distinct    */
-/* from every Q label (reading R4: one label per run, not per point).  Then  */
-/* a new clump starts wherever the label changes between consecutive points. */
-/* P[i] receives the 0-based clump of sample i; returns the number k of      */
-/* clumps.  Clumps are numbered in increasing u.                             */
+/* Definition used here: walk the points in increasing u.  A tie run (the    */
+/* maximal set of consecutive points sharing one u-value) must stay inside   */
+/* one clump.  A run whose points all lie in the same row keeps that row as  */
+/* its label; a run spread over several rows gets a label of its own that    */
+/* no other run and no row shares (reading R4: one label for the whole run). */
+/* Clumps are then the maximal stretches of consecutive points with equal    */
+/* labels.  P[i] receives the 0-based clump of sample i (clumps numbered in  */
+/* increasing u); the return value is the number k of clumps.                */
 /* ------------------------------------------------------------------------ */
 
 int oracle_clumps(const double *u, const int *Q, int n, int *P)
 {
     if (n <= 0) return 0;
     int *order = (int *)malloc(sizeof(int) * (size_t)n);
-    long *qt = (long *)malloc(sizeof(long) * (size_t)n);
-    if (!order || !qt) { free(order); free(qt); return -ORACLE_E_NOMEM; }
+    long *label = (long *)malloc(sizeof(long) * (size_t)n);
+    if (!order || !label) { free(order); free(label); return -ORACLE_E_NOMEM; }
     argsort(u, n, order);
-    for (int p = 0; p < n; p++) qt[p] = (long)Q[order[p]];
 
-    long fresh = -1;            /* fresh labels are negative: never a Q label */
-    int i = 0;
-    while (i < n) {
-        int s = 0;
-        int flag = 0;
-        for (int j = i + 1; j < n && u[order[j]] == u[order[i]]; j++) {
-            s += 1;
-            if (qt[j] != qt[i]) flag = 1;
-        }
-        if (s != 0 && flag) {
-            for (int j = 0; j <= s; j++) qt[i + j] = fresh;
-            fresh -= 1;
-        }
-        i += s + 1;
+    /* label of every sorted position, one tie run at a time */
+    long runs = 0;
+    int a = 0;
+    while (a < n) {
+        int b = a + 1;
+        while (b < n && u[order[b]] == u[order[a]]) b++;
+        int one_row = 1;
+        for (int p = a + 1; p < b; p++)
+            if (Q[order[p]] != Q[order[a]]) one_row = 0;
+        runs += 1;
+        /* rows are >= 0, so a negative run number never equals a row */
+        long lab = one_row ? (long)Q[order[a]] : -runs;
+        for (int p = a; p < b; p++) label[p] = lab;
+        a = b;
     }
 
-    int id = 0;
-    P[order[0]] = 0;
-    for (int p = 1; p < n; p++) {
-        if (qt[p] != qt[p - 1]) id += 1;
-        P[order[p]] = id;
+    /* a new clump wherever the label changes */
+    int clump = 0;
+    for (int p = 0; p < n; p++) {
+        if (p > 0 && label[p] != label[p - 1]) clump += 1;
+        P[order[p]] = clump;
     }
     free(order);
-    free(qt);
-    return id + 1;
+    free(label);
+    return clump + 1;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -450,6 +450,88 @@ def test_batch_equals_single():
 
 # ------------------------------------------------- readings of silent points
 
+def _three_level_pair(sizes, seed):
+    """A noiseless pair built on a variable with three distinct values: V
+    takes 0, 1, 2 on groups of the given sizes (shuffled), U = 10 V + 3 (the
+    same order, so both variables have the same three tie groups)."""
+    rng = np.random.default_rng(seed)
+    v = np.repeat(np.arange(3, dtype=np.float64), sizes)
+    v = v[rng.permutation(len(v))]
+    return 10.0 * v + 3.0, v
+
+
+def _h(probs):
+    return -sum(p * math.log(p) for p in probs if p > 0)
+
+
+@pytest.mark.parametrize("sizes", [(100, 100, 100), (50, 120, 130), (40, 200, 60)])
+def test_normalisation_uses_yhat(sizes):
+    """Appendix item 4: I(x, y) is normalised by min(log x, log yhat), yhat
+    being the number of rows EquipartitionYAxis actually used.  V takes three
+    values on groups of the given sizes and U = 10 V + 3, so both variables
+    have the same three tie groups G and every column partition is a function
+    of G.  In either orientation (the two are the same here):
+      y >= 3 rows: yhat = 3, the rows are G, the clumps are G; I(l) = H(G)
+        for l >= 3 and, for l = 2, the better of the two cuts of G;
+      y = 2 rows: the greedy rule merges two neighbouring groups (closed form
+        below), the clumps are those two rows, so I(l) = H(rows) (reading R7);
+    each divided by log min(l, yhat), and M(x, y) the larger of the two
+    orientations' (x, y) and (y, x) entries.  Mutual informations are the
+    textbook sum, not the oracle's entropy form.  Dividing by log min(x, y)
+    instead would lower every cell with x, y >= 4."""
+    n = sum(sizes)
+    u, v = _three_level_pair(sizes, seed=sum(sizes) + sizes[0])
+    for y in range(3, 16):
+        Q, yhat = oracle.equipartition(v, y)
+        assert yhat == 3
+    r = oracle.score_pair(u, v, 0.6, 15)
+    B = r["B"]
+    assert r["status"] == 0 and B == oracle.B_of(n, 0.6) == 30
+    grp = np.round(v).astype(int)
+    # 2-row equipartition of three groups: the second group opens row 2 iff
+    # |s1 + s2 - n/2| >= |s1 - n/2|, else the third one does
+    d = n / 2.0
+    rows2 = (grp >= 1) if abs(sizes[0] + sizes[1] - d) >= abs(sizes[0] - d) else (grp >= 2)
+    rows2 = rows2.astype(int)
+    Q2, yhat2 = oracle.equipartition(v, 2)
+    assert yhat2 == 2 and np.array_equal(Q2, rows2)
+    h_g = textbook_mi(grp, grp)
+    h_cut = max(textbook_mi((grp >= 1).astype(int), grp), textbook_mi((grp >= 2).astype(int), grp))
+    h_rows2 = textbook_mi(rows2, rows2)
+
+    def m_o(l, y):
+        if y >= 3:
+            return (h_g if l >= 3 else h_cut) / math.log(min(l, 3))
+        return h_rows2 / math.log(2)
+
+    cells = oracle.cell_layout(B)
+    assert (4, 4) in cells and (5, 6) in cells
+    want = np.array([max(m_o(x, y), m_o(y, x)) for x, y in cells])
+    assert np.max(np.abs(r["M"] - want)) <= 1e-12
+    assert abs(r["mic"] - want.max()) <= 1e-12
+    assert abs(r["mas"]) <= 1e-12
+    mcn = min(x * y for (x, y), m in zip(cells, r["M"]) if m >= r["mic"])
+    assert r["mcn_xy"] == mcn
+
+
+def test_normalisation_yhat_hand_value():
+    """A cell computed by hand where yhat < y decides the value: V has three
+    values on 4, 4 and 8 of n = 16 points and U = V.  With alpha = 1, B = 16.
+    For y = 4 rows the greedy rule keeps one row per group (d = 4: the second
+    group opens a row since |4 + 4 - 4| >= |4 - 4|, the third since
+    |4 + 8 - 4| >= |4 - 4| with d = 12/3), so yhat = 3; the three clumps give
+    I(4, 4) = H(1/4, 1/4, 1/2) = 1.5 ln 2 and M(4, 4) = 1.5 ln 2 / ln 3 =
+    0.9464..., where log min(4, 4) would give 0.75."""
+    v = np.array([0.0] * 4 + [1.0] * 4 + [2.0] * 8)
+    Q, yhat = oracle.equipartition(v, 4)
+    assert yhat == 3
+    r = oracle.score_pair(v.copy(), v, 1.0, 15)
+    assert r["B"] == 16
+    idx = {c: i for i, c in enumerate(oracle.cell_layout(16))}
+    assert abs(r["M"][idx[(4, 4)]] - 1.5 * math.log(2) / math.log(3)) <= 1e-12
+    assert abs(r["M"][idx[(3, 4)]] - 1.5 * math.log(2) / math.log(3)) <= 1e-12
+
+
 def test_khat_bound_is_cx():
     """Appendix item 7: the superclump count stops at khat = c*x (MINE.jar's
     c*x + 1 is the defect the paper reports).  Alternating rows on distinct x
