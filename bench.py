@@ -34,6 +34,9 @@ C = 15.0
 N_SAMPLES = 1340
 N_VARS = 2000
 L2_FLUSH_BYTES = 256 << 20
+# FP64 instructions an SM issues per clock on GB300 (its nominal 1.25 TFLOP/s
+# of FP64 FMA at about 2.07 GHz over 152 SMs: 1.25e12 / 2 / 152 / 2.07e9 = 2)
+FP64_PER_SM_CLK = 2
 
 
 def parse():
@@ -44,8 +47,9 @@ def parse():
     ap.add_argument("--impl", default="gmine", choices=["gmine", "reference"])
     ap.add_argument("--vars", type=int, default=N_VARS,
                     help="variables of the all-pairs workload (2000 = the metric's workload)")
-    ap.add_argument("--fp64-vars", type=int, default=200,
-                    help="variables whose all pairs time the plain FP64 path")
+    ap.add_argument("--fp64-vars", type=int, default=632,
+                    help="variables whose all pairs time the plain FP64 path (632: 10 %% of "
+                         "the metric workload's pairs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -297,30 +301,42 @@ def main():
     ms_step_max = max_over_ranks(ms_step, dist, dev)
     value = world * npairs / (ms_step_max / 1e3)
 
-    # the plain FP64 DP on all pairs of the first fp64_vars variables
+    # the plain FP64 DP on all pairs of the first fp64_vars variables: one
+    # warm-up on a small subset, then the mean of two timed steps, each with
+    # the DP launches timed by the library and their candidates counted
     fp64 = None
     if args.fp64_vars > 1:
         sub = min(args.fp64_vars, p)
         Ps = torch.from_numpy(gmine_all_pairs(sub)).to(dev)
         ws64 = gmine.Workspace(p, n, Ps.shape[0], ALPHA, C, gmine.PLAIN_FP64, device=dev)
         sc64 = torch.empty((Ps.shape[0], gmine.SCORE_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        m64 = gmine.Measure(device=dev)
 
-        def step64():
-            rc = gmine.lib().gmine_compute_batch(
-                gmine._dptr(Vd), p, n, gmine._dptr(Ps), Ps.shape[0],
+        def step64(npairs64, measure):
+            rc = gmine.lib().gmine_compute_batch_ex(
+                gmine._dptr(Vd), p, n, gmine._dptr(Ps), npairs64,
                 gmine.ctypes.byref(gmine.Param(ALPHA, C)), gmine.PLAIN_FP64, ws64.ptr, ws64.nbytes,
-                gmine._dptr(sc64), None, gmine._stream_ptr(stream))
-            gmine._check(rc, "gmine_compute_batch")
-        step64()
+                gmine._dptr(sc64), None, gmine.ctypes.byref(m64.trace) if measure else None,
+                gmine._stream_ptr(stream))
+            gmine._check(rc, "gmine_compute_batch_ex")
+        step64(min(Ps.shape[0], 780), False)
         torch.cuda.synchronize(dev)
-        e0.record(stream)
-        step64()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = e0.elapsed_time(e1)
-        fp64 = {"value": Ps.shape[0] / (ms64 / 1e3), "unit": "pairs/s",
-                "sample": "all %d pairs of the first %d variables, one step after one warm-up"
-                          % (Ps.shape[0], sub)}
+        ms64, dp64_ms, cand64, dp64_launches = 0.0, 0.0, 0, 0
+        for _ in range(2):
+            flush.zero_()
+            e0.record(stream)
+            step64(Ps.shape[0], True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms64 += e0.elapsed_time(e1) / 2
+            dp64_ms += m64.dp_ms / 2
+            dp64_launches += m64.dp_launches
+            cand64 += int(m64.counters[0].item()) // 2
+        fp64 = {"value": Ps.shape[0] / (ms64 / 1e3), "unit": "pairs/s", "ms_per_step": ms64,
+                "sample": "all %d pairs of the first %d variables (%.1f %% of the workload's pairs), "
+                          "mean of 2 steps after a warm-up" % (Ps.shape[0], sub, 100.0 * Ps.shape[0] / npairs),
+                "dp_candidates_per_step": cand64, "dp_kernel_ms_per_step": dp64_ms,
+                "dp_launches_per_step": dp64_launches // 2}
         del ws64
 
     # Pearson rho and the non-linearity index MIC - rho^2 of every pair of
@@ -363,14 +379,17 @@ def main():
                 gmine.ctypes.c_void_p(hs.data_ptr()), None, gmine._stream_ptr(stream))
             gmine._check(rc, "gmine_compute_batch_host")
         step_host()
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        step_host()
-        e2e_s = time.perf_counter() - t0
+        e2e_s = 0.0
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            step_host()
+            e2e_s += (time.perf_counter() - t0) / 2
         e2e = {"value": world * npairs / e2e_s, "unit": "pairs/s",
                "h2d_bytes_per_step": int(V.nbytes + P.nbytes),
-               "d2h_bytes_per_step": int(npairs * gmine.SCORE_DTYPE.itemsize)}
+               "d2h_bytes_per_step": int(npairs * gmine.SCORE_DTYPE.itemsize),
+               "calls": "mean of 2 host-buffer calls after one warm-up call"}
         del wsh
 
     cpu = None
@@ -412,11 +431,23 @@ def main():
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
-    # one subtract (FADD) and one max (FMNMX) per DP step on the 128 FP32
-    # lanes of each SM at the maximum SM clock
-    peak = sms * 128 * fmax * 1e6 / 2.0 / 1e12
+    # ALU ceiling of the float DP: a candidate costs half a packed
+    # subtraction (sub.f32x2 forms two) and half a three-operand max (one
+    # merges two candidates into a running maximum): one instruction per
+    # candidate on the 128 FP32 lanes of each SM at the maximum SM clock
+    peak = sms * 128 * fmax * 1e6 / 1.0 / 1e12
     dp_launch_ms = dp_ms / max(dp_launches, 1)
     achieved = (cand / max(dp_launches, 1)) / (dp_launch_ms / 1e3) / 1e12 if dp_ms > 0 else 0.0
+    if fp64 is not None:
+        # ALU ceiling of the double DP: one DADD and one DMNMX per candidate
+        # on the FP64 pipe, FP64_PER_SM_CLK of them per SM and clock
+        peak64 = sms * FP64_PER_SM_CLK * fmax * 1e6 / 2.0 / 1e12
+        ach64 = (fp64["dp_candidates_per_step"] / (fp64["dp_kernel_ms_per_step"] / 1e3) / 1e12
+                 if fp64["dp_kernel_ms_per_step"] > 0 else 0.0)
+        fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "Tcand/s",
+                            "frac": ach64 / peak64,
+                            "peak_basis": "%d SMs x %d FP64 instr/clk x %.0f MHz / 2 instr per DP step "
+                                          "(DADD + DMNMX)" % (sms, FP64_PER_SM_CLK, fmax)}
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -431,8 +462,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcand/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
                          "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_warp, k_dp_mid, k_dp_small, k_dp_two)",
-                         "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr per DP step"
-                                       % (sms, fmax),
+                         "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 1 instr per DP step "
+                                       "(half a packed sub.f32x2 + half a 3-operand max)" % (sms, fmax),
                          "dp_candidates_per_step": cand // max(args.steps, 1),
                          "dp_kernel_ms_per_step": dp_ms / args.steps,
                          "dp_launches_per_step": dp_launches // args.steps,

@@ -31,6 +31,12 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls taking d_* pointers only enqueue work on it and
  *     return; results are ready once the stream has been synchronised.
+ *     The batch calls also copy a small table (B(m) = floor(m^alpha), made
+ *     with the host's pow) from host memory with cudaMemcpyAsync on it.
+ *   - Several host threads may call the library at once, each with its own
+ *     workspace and stream: the shared-memory limits the calls set on the
+ *     kernels only ever grow, so one call's planning never lowers what
+ *     another call's launches need.
  *   - Every call returns an int status (GMINE_OK = 0 or a GMINE_E_* code);
  *     nothing aborts or throws across this boundary.  A per-pair status is
  *     also stored in each gmine_pair_score.
@@ -62,8 +68,7 @@ extern "C" {
 #define GMINE_E_ARG 5        /* NULL pointer, negative size, bad index */
 #define GMINE_E_WORKSPACE 6  /* workspace smaller than gmine_plan reported */
 #define GMINE_E_CUDA 7       /* a CUDA runtime call failed */
-#define GMINE_E_LIMIT 8      /* a size beyond what this build supports (n > 131072; the plain FP64
-                                path above 65535 samples) */
+#define GMINE_E_LIMIT 8      /* a size beyond what this build supports (n > 131072) */
 #define GMINE_E_NODEVICE 9   /* no usable CUDA device */
 
 /* precision of the OptimizeXAxis dynamic program */
@@ -188,6 +193,53 @@ int gmine_compute_batch_host(const double *h_vars, int64_t p, int64_t n,
                              gmine_pair_score *h_scores, double *h_M,
                              void *stream);
 
+/* ---- batches of uneven pairs ------------------------------------------- */
+
+/* Largest number of distinct alpha values in one uneven batch. */
+#define GMINE_MAX_ALPHAS 8
+
+/* Sizes for gmine_compute_batch_uneven (same arguments as its call):
+   *m_cells_per_pair: cells of M reserved per pair, those of
+   B = floor(n^max alpha); *workspace_bytes: the workspace to pass (a few
+   GB for large n and alpha: the records of a chunk of heavy pairs take up
+   to 24 GiB).  Errors: GMINE_E_ARG (NULL h_alphas, n_alphas < 1, negative
+   sizes), GMINE_E_PARAM (an alpha outside (0, 1] or c not finite and > 0),
+   GMINE_E_LIMIT (n_alphas > GMINE_MAX_ALPHAS or n > 131072). */
+int gmine_plan_uneven(int64_t p, int64_t n, int64_t n_pairs, const double *h_alphas,
+                      int32_t n_alphas, double c, int32_t precision,
+                      int64_t *m_cells_per_pair, int64_t *workspace_bytes);
+
+/* mine_compute_score over pairs of uneven size, each with its own alpha:
+   pair i uses the n_i samples where both its variables are finite and
+   B_i = floor(n_i^alpha_i) (Sec. 2C: B(n) = n^alpha, per pair), with the
+   same steps and kernels as gmine_compute_batch.
+   - d_vars [p][n] double, shorter variables padded with NaN; d_pairs
+     [n_pairs][2] int32; both device memory.
+   - h_alphas: host array of the n_alphas distinct alpha values (1 ..
+     GMINE_MAX_ALPHAS); d_alpha_idx: device uint8 [n_pairs], pair i takes
+     h_alphas[d_alpha_idx[i]] (NULL allowed when n_alphas == 1).
+   - d_scores [n_pairs] and d_M [n_pairs * m_cells_per_pair] (or NULL) as for
+     gmine_compute_batch: pair i's score at i, its cells at i *
+     m_cells_per_pair.
+   - trace: NULL, or only the counters and timing fields set (d_counters,
+     h_dp_ms, h_dp_launches, h_kernel_launches); per-task arrays are refused.
+   How it runs: the pairs' alpha indices and sample counts are read back to
+   the host (the call synchronises `stream` twice), the pairs are ordered by
+   their DP work, heaviest first, and cut into chunks that fit the
+   workspace, each planned for its own largest n and B; each pair gets its
+   own compacted ranks.  A pair's result does not depend on the rest of
+   the batch.  Returns once the last chunk is enqueued.
+   Errors: GMINE_E_ARG (NULL pointers, an alpha index >= n_alphas, per-task
+   trace arrays), GMINE_E_PARAM, GMINE_E_LIMIT as gmine_plan_uneven,
+   GMINE_E_WORKSPACE, GMINE_E_CUDA; per-pair statuses as gmine_compute_batch. */
+int gmine_compute_batch_uneven(const double *d_vars, int64_t p, int64_t n,
+                               const int32_t *d_pairs, int64_t n_pairs,
+                               const double *h_alphas, int32_t n_alphas,
+                               const uint8_t *d_alpha_idx, double c, int32_t precision,
+                               void *d_workspace, int64_t workspace_bytes,
+                               gmine_pair_score *d_scores, double *d_M,
+                               const gmine_trace *trace, void *stream);
+
 /* ---- batch without a caller workspace ---------------------------------- */
 
 /* gmine_compute_batch with the working memory taken from a fixed array
@@ -204,13 +256,18 @@ int gmine_compute_batch_host(const double *h_vars, int64_t p, int64_t n,
      at n ~ 1000, or one pair up to a few thousand samples at alpha = 0.6).
    - The first call on each device looks up the array's device address
      (cudaGetSymbolAddress with that device current) and keeps it; make that
-     first call before any stream capture.
+     first call before any stream capture.  A reset of the device
+     (cudaDeviceReset) after that first call is not supported: the kept
+     address would then be stale.
    - Every call on a device shares the one array.  Its contents from an
      earlier call do not matter (the computation initialises all it reads),
      but calls whose work can overlap on the GPU (other streams, other host
      threads) race on it: order them, e.g. on one stream.
-   The array stays allocated on every GPU where the call was used until the
-   process exits. */
+   The array is device code of the library: with lazy module loading (the
+   CUDA runtime's default) a device reserves its 64 MiB when this call first
+   runs there; with CUDA_MODULE_LOADING=EAGER every device on which the
+   process uses the CUDA runtime reserves it, whether or not the call runs.
+   Either way it stays reserved until the process exits. */
 int gmine_compute_batch_static(const double *d_vars, int64_t p, int64_t n,
                                const int32_t *d_pairs, int64_t n_pairs,
                                const gmine_param *param, int32_t precision,

@@ -56,6 +56,10 @@ def lib():
                                          ctypes.c_double, _dp, _ip, _ip, _dp,
                                          _lp, ctypes.c_int]
         L.oracle_score_batch.restype = ctypes.c_int
+        L.oracle_score_batch_alphas.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip,
+                                                ctypes.c_long, _dp, ctypes.c_double, _dp, _ip,
+                                                _ip, _dp, _lp, ctypes.c_int]
+        L.oracle_score_batch_alphas.restype = ctypes.c_int
         L.oracle_pearson.argtypes = [_dp, _dp, ctypes.c_int, _ip]
         L.oracle_pearson.restype = ctypes.c_double
         L.oracle_max_threads.argtypes = []
@@ -172,6 +176,7 @@ def score_pair(x, y, alpha=0.6, c=15.0):
 
 def score_batch(vars_, pairs, alpha=0.6, c=15.0, nthreads=0, want_M=False):
     """All listed pairs of the rows of vars_ ([p, n]); OpenMP over pairs.
+    alpha: one value, or one per pair (B = n^alpha of each pair, Sec. 2C).
 
     Returns dict(stats [npairs, 4], info [npairs, 6], status [npairs],
     M (concatenated cells) and M_offsets when want_M)."""
@@ -179,6 +184,8 @@ def score_batch(vars_, pairs, alpha=0.6, c=15.0, nthreads=0, want_M=False):
     p, n = vars_.shape
     pairs = _i(pairs).reshape(-1, 2)
     npairs = pairs.shape[0]
+    per_pair = np.ndim(alpha) > 0
+    alphas = _d(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (npairs,)))
     stats = np.zeros((npairs, 4), dtype=np.float64)
     info = np.zeros((npairs, 6), dtype=np.int32)
     status = np.zeros(npairs, dtype=np.int32)
@@ -187,17 +194,19 @@ def score_batch(vars_, pairs, alpha=0.6, c=15.0, nthreads=0, want_M=False):
     if want_M:
         fin = np.isfinite(vars_)
         nu = (fin[pairs[:, 0]] & fin[pairs[:, 1]]).sum(axis=1)
-        cells = np.array([m_cells(B_of(max(int(m), 1), alpha)) for m in nu], dtype=np.int64)
+        cells = np.array([m_cells(B_of(max(int(m), 1), a)) for m, a in zip(nu, alphas)], dtype=np.int64)
         offs = np.zeros(npairs, dtype=np.int64)
         if npairs:
             offs[1:] = np.cumsum(cells)[:-1]
         M = np.zeros(max(int(cells.sum()), 1), dtype=np.float64)
-    rc = lib().oracle_score_batch(
-        _pd(vars_), p, n, _pi(pairs), npairs, float(alpha), float(c),
-        _pd(stats), _pi(info), _pi(status),
-        _pd(M) if M is not None else None,
-        offs.ctypes.data_as(_lp) if offs is not None else None,
-        int(nthreads))
+    args = (_pd(stats), _pi(info), _pi(status), _pd(M) if M is not None else None,
+            offs.ctypes.data_as(_lp) if offs is not None else None, int(nthreads))
+    if per_pair:
+        rc = lib().oracle_score_batch_alphas(_pd(vars_), p, n, _pi(pairs), npairs, _pd(alphas),
+                                             float(c), *args)
+    else:
+        rc = lib().oracle_score_batch(_pd(vars_), p, n, _pi(pairs), npairs, float(alpha),
+                                      float(c), *args)
     if rc != 0:
         raise ValueError("oracle_score_batch: " + STATUS.get(rc, str(rc)))
     out = {"stats": stats, "info": info, "status": status}

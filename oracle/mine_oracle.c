@@ -518,10 +518,62 @@ int oracle_score_pair(const double *x, const double *y, int n, double alpha,
 /* ------------------------------------------------------------------------ */
 /* A batch of pairs of variables: vars is [p][n] row-major (one variable per */
 /* row, as in the paper's variables-by-samples files); pairs is [npairs][2]. */
-/* M_offsets[i] is where pair i's cells start in M (or M is NULL).           */
-/* stats is [npairs][4], info [npairs][6], status [npairs].  Pairs are       */
-/* independent and are spread over nthreads OpenMP threads.                  */
+/* Pair i uses alphas[i] when alphas is not NULL, else alpha (B = n^alpha is */
+/* a per-pair quantity, Sec. 2C).  M_offsets[i] is where pair i's cells     */
+/* start in M (or M is NULL).  stats is [npairs][4], info [npairs][6],      */
+/* status [npairs].  Pairs are independent and are spread over nthreads     */
+/* OpenMP threads.                                                          */
 /* ------------------------------------------------------------------------ */
+
+static void score_one(const double *vars, int n, const int *pairs, long i, double alpha,
+                      double c, double *stats, int *info, int *status, double *M,
+                      const long *M_offsets, double **Mbuf, int *cap)
+{
+    const double *xv = vars + (size_t)pairs[2 * i] * (size_t)n;
+    const double *yv = vars + (size_t)pairs[2 * i + 1] * (size_t)n;
+    int need = oracle_m_cells(oracle_B(n, alpha));
+    if (need > *cap) {
+        free(*Mbuf);
+        *cap = need;
+        *Mbuf = (double *)malloc(sizeof(double) * (size_t)*cap);
+    }
+    status[i] = oracle_score_pair(xv, yv, n, alpha, c, *Mbuf, stats + 4 * i, info + 6 * i);
+    if (M && M_offsets)
+        memcpy(M + M_offsets[i], *Mbuf, sizeof(double) * (size_t)info[6 * i + 3]);
+}
+
+static int score_batch(const double *vars, int n, const int *pairs, long npairs,
+                       double alpha, const double *alphas, double c, double *stats,
+                       int *info, int *status, double *M, const long *M_offsets,
+                       int nthreads)
+{
+    for (long i = 0; i < npairs; i++) {
+        int rc = oracle_check_param(alphas ? alphas[i] : alpha, c);
+        if (rc != ORACLE_OK) return rc;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+        int cap = 1 << 12;
+        double *Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+        for (long i = 0; i < npairs; i++)
+            score_one(vars, n, pairs, i, alphas ? alphas[i] : alpha, c, stats, info, status, M,
+                      M_offsets, &Mbuf, &cap);
+        free(Mbuf);
+    }
+#else
+    (void)nthreads;
+    int cap = 1 << 12;
+    double *Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
+    for (long i = 0; i < npairs; i++)
+        score_one(vars, n, pairs, i, alphas ? alphas[i] : alpha, c, stats, info, status, M,
+                  M_offsets, &Mbuf, &cap);
+    free(Mbuf);
+#endif
+    return ORACLE_OK;
+}
 
 int oracle_score_batch(const double *vars, int p, int n, const int *pairs,
                        long npairs, double alpha, double c, double *stats,
@@ -531,48 +583,18 @@ int oracle_score_batch(const double *vars, int p, int n, const int *pairs,
     (void)p;
     int rc = oracle_check_param(alpha, c);
     if (rc != ORACLE_OK) return rc;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel
-    {
-        int cap = 1 << 12;
-        double *Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
-#pragma omp for schedule(dynamic, 1)
-        for (long i = 0; i < npairs; i++) {
-            const double *xv = vars + (size_t)pairs[2 * i] * (size_t)n;
-            const double *yv = vars + (size_t)pairs[2 * i + 1] * (size_t)n;
-            int need = oracle_m_cells(oracle_B(n, alpha));
-            if (need > cap) {
-                free(Mbuf);
-                cap = need;
-                Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
-            }
-            status[i] = oracle_score_pair(xv, yv, n, alpha, c, Mbuf, stats + 4 * i, info + 6 * i);
-            if (M && M_offsets)
-                memcpy(M + M_offsets[i], Mbuf, sizeof(double) * (size_t)info[6 * i + 3]);
-        }
-        free(Mbuf);
-    }
-#else
-    (void)nthreads;
-    int cap = 1 << 12;
-    double *Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
-    for (long i = 0; i < npairs; i++) {
-        const double *xv = vars + (size_t)pairs[2 * i] * (size_t)n;
-        const double *yv = vars + (size_t)pairs[2 * i + 1] * (size_t)n;
-        int need = oracle_m_cells(oracle_B(n, alpha));
-        if (need > cap) {
-            free(Mbuf);
-            cap = need;
-            Mbuf = (double *)malloc(sizeof(double) * (size_t)cap);
-        }
-        status[i] = oracle_score_pair(xv, yv, n, alpha, c, Mbuf, stats + 4 * i, info + 6 * i);
-        if (M && M_offsets)
-            memcpy(M + M_offsets[i], Mbuf, sizeof(double) * (size_t)info[6 * i + 3]);
-    }
-    free(Mbuf);
-#endif
-    return ORACLE_OK;
+    return score_batch(vars, n, pairs, npairs, alpha, NULL, c, stats, info, status, M,
+                       M_offsets, nthreads);
+}
+
+int oracle_score_batch_alphas(const double *vars, int p, int n, const int *pairs,
+                              long npairs, const double *alphas, double c, double *stats,
+                              int *info, int *status, double *M, const long *M_offsets,
+                              int nthreads)
+{
+    (void)p;
+    return score_batch(vars, n, pairs, npairs, 0.0, alphas, c, stats, info, status, M,
+                       M_offsets, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "gmine.h"
@@ -102,34 +104,53 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   S.xmax = std::max(tb.xmax, 2);
   const int64_t rbytes = (int64_t)(tb.kmax + 1) * S.LS * rs;
   const int64_t lbytes = (int64_t)(n + 1) * rs;
-  // traceback scratch aliased on the X buffers once the DP is done
-  // (cuts of up to eight paths per warp, I(l), l*(l))
-  const int64_t cuts_b = (4LL * 8 * NW * S.xmax + 15) & ~int64_t(15);
+  // traceback scratch aliased on the X buffers once the DP is done (cuts of
+  // up to eight paths per warp on the float path, one on the double path;
+  // I(l); l*(l))
+  const int64_t cuts_b = (4LL * (fp32 ? 8 : 1) * NW * S.xmax + 15) & ~int64_t(15);
   const int64_t I_b = (8LL * (S.xmax + 1) + 15) & ~int64_t(15);
   const int64_t lst_b = 4LL * (S.xmax + 1);
+  const int64_t tb_bytes = cuts_b + I_b + lst_b;
   S.off_I_rel = (int)cuts_b;
   S.off_lst_rel = (int)(cuts_b + I_b);
-  const int64_t xbytes = std::max<int64_t>((int64_t)2 * 32 * S.LX * rs, cuts_b + I_b + lst_b);
-  int64_t fixed = 0;
-  auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
-  S.off_X = add(xbytes);
-  S.off_Eb = add((int64_t)(32 * 31 / 2) * rs);  // the in-block triangle
-  S.off_rbuf = add((int64_t)2 * 32 * rs);
-  S.off_Rtop = add((int64_t)rs);  // R(k, lmax)
+  const int64_t xrows = (int64_t)2 * 32 * S.LX * rs;
   const int64_t sdbytes = 4LL * std::max(tb.sd_max, 4);
-  const int64_t before_sd = fixed;
-  S.off_sd = add(sdbytes);
-  S.sd_scr_off = -1;
   const int reserve = 1024;
+  // Shared memory: the X rows (or the traceback scratch aliased on them),
+  // the in-block triangle, two R buffers of 32, R(k, lmax), the superclump
+  // rows; with room for it, also the L table and the R table.
+  auto place = [&](bool x_smem, bool sd_smem) -> int64_t {
+    int64_t fixed = 0;
+    auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
+    S.off_X = x_smem ? add(std::max<int64_t>(xrows, tb_bytes)) : -1;
+    S.off_tb = x_smem ? S.off_X : add(tb_bytes);
+    S.off_Eb = add((int64_t)(32 * 31 / 2) * rs);  // the in-block triangle
+    S.off_rbuf = add((int64_t)2 * 32 * rs);
+    S.off_Rtop = add((int64_t)rs);  // R(k, lmax)
+    S.off_sd = sd_smem ? add(sdbytes) : -1;
+    return fixed;
+  };
+  int64_t fixed = place(true, true);
   const bool in_smem = fixed + rbytes + lbytes + 32 + reserve <= smem_optin;
   *r_in_smem = in_smem;
+  // The CTA's global scratch: the R table (one spare row), then what does
+  // not fit in shared memory.  The X rows go first (each is touched once
+  // per level and block), the superclump rows only if they still do not fit
+  // (they are read for every entropy term).
+  int64_t scr = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+  S.x_scr_off = -1;
+  S.sd_scr_off = -1;
   if (!in_smem && fixed + reserve > smem_optin) {
-    // the superclump rows do not fit beside the X rows either (very large
-    // k): they go to the CTA's global scratch after the R table
-    fixed = before_sd;
-    S.off_sd = -1;
-    S.sd_scr_off = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
+    fixed = place(false, true);
+    S.x_scr_off = scr;
+    scr = align256(scr + xrows);
+    if (fixed + reserve > smem_optin) {
+      fixed = place(false, false);
+      S.sd_scr_off = scr;
+      scr = align256(scr + sdbytes);
+    }
   }
+  S.scr_bytes = in_smem ? 0 : scr;
   int64_t o = fixed;
   if (in_smem) {
     S.off_L = (int)o;
@@ -260,28 +281,46 @@ struct DPGroup {
   int64_t scratch_per_cta, o_scratch;
 };
 
-// Workspace layout of a batch (byte offsets from the workspace base).
-struct Layout {
-  int64_t n, p, n_pairs, chunk, slots;
+// Kernel plan of a chunk of pairs that have at most n used samples each
+// and B <= Bc: DP launch groups, partition and sort placement, record sizes.
+struct ChunkPlan {
+  int64_t n;
   int B;
   TaskBounds tb;        // all row counts
   int ngroups;
   DPGroup grp[kMaxDPGroups];
   PartPlan part;
   int part_ctas;
-  int64_t o_partscr;     // partition regions in global memory (large n), or -1
+  bool part_global;      // partition regions in global memory (large n)
   bool part_wide;        // 32-bit positions in the partition (n > 65535)
-  int64_t o_rankscr;     // sort keys in global memory (large n), or -1
-  int rank_ctas, rank_smem_bytes;
+  int rank_ctas, rank_smem_bytes;  // rank_ctas > 0: sort keys in global scratch
   int64_t rank_scr_per_cta;
-  int64_t rec_per_orient;
-  int64_t cells_max;
+  int64_t rec_per_orient;  // ints of the task records of one (pair, orientation)
+  int64_t cells;           // cells of M for B
+  int R, bstride;          // equipartitions per slot: y = 2 .. R + 1, bounds stride
+};
+
+// Workspace layout of a batch (byte offsets from the workspace base).
+struct Layout {
+  int64_t n, p, n_pairs, chunk, slots;
+  ChunkPlan cp;          // every chunk's plan (regular batches); the largest (uneven)
+  int64_t o_partscr;     // partition regions in global memory, or -1
+  int64_t partscr_bytes;
+  int64_t o_rankscr;     // sort keys in global memory, or -1
+  int64_t rankscr_bytes;
   int64_t o_Btab, o_L64, o_L32, o_lnt, o_recoff, o_nf;
   int64_t o_perm, o_pos, o_grp, o_gstart, o_ngroups, o_nslot;
   int64_t o_bounds, o_yhat;
   int64_t o_slot, o_nused, o_Bp, o_flags, o_dirty, o_ndirty;
   int64_t o_rec, o_Mo, o_queue;
   int64_t o_hvars, o_hpairs, o_hscores, o_hM;
+  // uneven batches: one region each for the per-slot rank arrays, the
+  // equipartitions, the records and M_o, whose layout each chunk sets for
+  // its own sizes; the per-pair counts copied to the host; the pair order
+  bool uneven;
+  int n_tables;          // B tables (one per alpha, then the largest alpha's)
+  int64_t o_rank, rank_bytes, o_equi, equi_bytes, rec_bytes, Mo_bytes, o_dpscr, dpscr_bytes;
+  int64_t o_count, o_order;
   int64_t total;
 };
 
@@ -291,14 +330,10 @@ int dp_occupancy(bool fp32, bool rsm, int lev, int smem, int threads, int* block
   return GMINE_OK;
 }
 
-int64_t dp_scratch(const TaskBounds& tb, const DPPlan& S, bool fp32, bool r_smem) {
-  const int rs = fp32 ? 4 : 8;
-  // one spare row: a level group may read past the last row's columns;
-  // then the superclump rows when they do not fit in shared memory
-  if (r_smem) return 0;
-  const int64_t r = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
-  return S.off_sd < 0 ? align256(r + 4LL * std::max(tb.sd_max, 4)) : r;
-}
+// Global scratch of one CTA of the blocked DP: the R table (with one spare
+// row: a level group may read past the last row's columns), then the
+// superclump rows and the X rows when they do not fit in shared memory.
+int64_t dp_scratch(const DPPlan& S, bool r_smem) { return r_smem ? 0 : S.scr_bytes; }
 
 // CUDA events around the DP launches of one call (h_dp_ms of gmine_trace).
 struct DPTiming {
@@ -331,46 +366,36 @@ struct DPTiming {
   }
 };
 
-int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
-                int32_t flags, Layout* L) {
-  if (!param) return GMINE_E_ARG;
-  if (gmine_check_param(param) != GMINE_OK) return GMINE_E_PARAM;
-  if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
-  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
-  if (n > kMaxN) return GMINE_E_LIMIT;
-  DeviceInfo dev;
-  int rc = device_info(&dev);
-  if (rc != GMINE_OK) return rc;
-  *L = Layout{};
-  L->n = n;
-  L->p = p;
-  L->n_pairs = n_pairs;
-  L->B = n > 0 ? host_B(n, param->alpha) : 0;
-  const int B = L->B;
-  L->tb = task_bounds((int)n, B, param->c, 2, B / 2);
-  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
-  // DP launch groups: consecutive row counts whose x - 1 share a level group
-  L->ngroups = 0;
+// The kernel plan of a chunk whose pairs have at most n used samples and B
+// at most Bc (tasks y = 2 .. Bc/2), clump factor c.
+int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, ChunkPlan* cp) {
+  *cp = ChunkPlan{};
+  cp->n = n;
+  cp->B = B;
+  int rc = GMINE_OK;
+  cp->tb = task_bounds((int)n, B, c, 2, B / 2);
+    // DP launch groups: consecutive row counts whose x - 1 share a level group
+  cp->ngroups = 0;
   for (int y = 2; y <= B / 2; ++y) {
     // x = 2 (one level above the first) has a kernel of its own; row counts
     // with few levels are grouped by x (each launch is planned for its own
     // task sizes)
     const int x = B / y;
     const int lev = x == 2 ? 2 : dp_level_group(fp32, std::max(x - 1, 1));
-    if (L->ngroups > 0 && L->grp[L->ngroups - 1].lev == lev &&
-        (lev > 4 || B / L->grp[L->ngroups - 1].ylo == x)) {
-      L->grp[L->ngroups - 1].yhi = y;
+    if (cp->ngroups > 0 && cp->grp[cp->ngroups - 1].lev == lev &&
+        (lev > 4 || B / cp->grp[cp->ngroups - 1].ylo == x)) {
+      cp->grp[cp->ngroups - 1].yhi = y;
     } else {
-      if (L->ngroups == kMaxDPGroups) return GMINE_E_LIMIT;
-      DPGroup& g = L->grp[L->ngroups++];
+      if (cp->ngroups == kMaxDPGroups) return GMINE_E_LIMIT;
+      DPGroup& g = cp->grp[cp->ngroups++];
       g = DPGroup{};
       g.ylo = g.yhi = y;
       g.lev = lev;
     }
   }
-  for (int gi = 0; gi < L->ngroups; ++gi) {
-    DPGroup& g = L->grp[gi];
-    const TaskBounds tg = task_bounds((int)n, B, param->c, g.ylo, g.yhi);
+  for (int gi = 0; gi < cp->ngroups; ++gi) {
+    DPGroup& g = cp->grp[gi];
+    const TaskBounds tg = task_bounds((int)n, B, c, g.ylo, g.yhi);
     if (g.lev == 2) {
       int blocks = 0;
       g.two = true;
@@ -473,19 +498,19 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       rc = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
       if (rc != GMINE_OK) return rc;
     }
-    g.scratch_per_cta = dp_scratch(tg, g.S, fp32, g.rsm);
+    g.scratch_per_cta = dp_scratch(g.S, g.rsm);
   }
-  for (int gi = 0; gi < L->ngroups; ++gi) {
+  for (int gi = 0; gi < cp->ngroups; ++gi) {
     // an instance of the blocked kernel can serve several groups (row counts
     // with four levels are split by x; a two-column group may fall back to
     // it): one attribute per instance (the largest plan of its groups), then
     // each group's occupancy at its own size
-    DPGroup& g = L->grp[gi];
+    DPGroup& g = cp->grp[gi];
     auto blocked = [](const DPGroup& h) { return !(h.two || h.warp || h.mid || h.small); };
     if (!blocked(g)) continue;
     int smax = 1;
-    for (int gj = 0; gj < L->ngroups; ++gj) {
-      const DPGroup& h = L->grp[gj];
+    for (int gj = 0; gj < cp->ngroups; ++gj) {
+      const DPGroup& h = cp->grp[gj];
       if (blocked(h) && h.rsm == g.rsm && h.lev == g.lev) smax = std::max(smax, h.S.total);
     }
     int blocks = 0;
@@ -499,12 +524,12 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
     // the warp-per-task kernel is shared by its groups: one attribute (the
     // largest plan), then each group's occupancy at its own size
     int smax = 0, mmax = 0;
-    for (int gi = 0; gi < L->ngroups; ++gi) {
-      if (L->grp[gi].small) smax = std::max(smax, L->grp[gi].SS.total);
-      if (L->grp[gi].mid) mmax = std::max(mmax, L->grp[gi].MS.total);
+    for (int gi = 0; gi < cp->ngroups; ++gi) {
+      if (cp->grp[gi].small) smax = std::max(smax, cp->grp[gi].SS.total);
+      if (cp->grp[gi].mid) mmax = std::max(mmax, cp->grp[gi].MS.total);
     }
-    for (int gi = 0; gi < L->ngroups; ++gi) {
-      DPGroup& g = L->grp[gi];
+    for (int gi = 0; gi < cp->ngroups; ++gi) {
+      DPGroup& g = cp->grp[gi];
       if (!g.mid) continue;
       int blocks = 0;
       cudaError_t e = dp_mid_configure(fp32, mmax, g.threads, &blocks, true);
@@ -513,15 +538,15 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       if (blocks < 1) return GMINE_E_LIMIT;
       g.ctas = blocks * dev.sms;
     }
-    for (int gi = 0; gi < L->ngroups; ++gi) {
+    for (int gi = 0; gi < cp->ngroups; ++gi) {
       // one attribute per warp-kernel instance (the largest plan of its
       // groups), then each group's occupancy at its own size
-      DPGroup& g = L->grp[gi];
+      DPGroup& g = cp->grp[gi];
       if (!g.warp) continue;
       int wmax = 0;
-      for (int gj = 0; gj < L->ngroups; ++gj)
-        if (L->grp[gj].warp && L->grp[gj].lev == g.lev && L->grp[gj].tdw == g.tdw)
-          wmax = std::max(wmax, L->grp[gj].WS.total);
+      for (int gj = 0; gj < cp->ngroups; ++gj)
+        if (cp->grp[gj].warp && cp->grp[gj].lev == g.lev && cp->grp[gj].tdw == g.tdw)
+          wmax = std::max(wmax, cp->grp[gj].WS.total);
       int blocks = 0;
       cudaError_t e = dp_warp_configure(g.lev, g.tdw, wmax, g.threads, &blocks, true);
       if (e == cudaSuccess) e = dp_warp_configure(g.lev, g.tdw, g.WS.total, g.threads, &blocks, false);
@@ -529,8 +554,8 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       if (blocks < 1) return GMINE_E_LIMIT;
       g.ctas = blocks * dev.sms;
     }
-    for (int gi = 0; gi < L->ngroups; ++gi) {
-      DPGroup& g = L->grp[gi];
+    for (int gi = 0; gi < cp->ngroups; ++gi) {
+      DPGroup& g = cp->grp[gi];
       if (!g.small) continue;
       int blocks = 0;
       cudaError_t e = dp_small_configure(fp32, smax, g.threads, &blocks);
@@ -540,57 +565,84 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
       g.ctas = blocks * dev.sms;
     }
   }
-  L->part = make_part_plan((int)n, L->tb, 4);
-  if (L->part.total + 1024 > dev.smem_optin) L->part = make_part_plan((int)n, L->tb, 1);
+  cp->part = make_part_plan((int)n, cp->tb, 4);
+  if (cp->part.total + 1024 > dev.smem_optin) cp->part = make_part_plan((int)n, cp->tb, 1);
   const bool part_wide = n > kMaxN16;  // 32-bit positions and counts
-  const bool part_global = part_wide || L->part.total + 1024 > dev.smem_optin;
-  if (part_global) L->part = make_part_plan((int)n, L->tb, 4);  // in global scratch
-  L->part_wide = part_wide;
+  const bool part_global = part_wide || cp->part.total + 1024 > dev.smem_optin;
+  cp->part_global = part_global;
+  if (part_global) cp->part = make_part_plan((int)n, cp->tb, 4);  // in global scratch
+  cp->part_wide = part_wide;
   {
     int pb = 0;
-    const int smem = part_global ? 0 : L->part.total;
-    cudaError_t e = partition_configure(part_global, part_wide, smem, 32 * L->part.warps, &pb);
+    const int smem = part_global ? 0 : cp->part.total;
+    cudaError_t e = partition_configure(part_global, part_wide, smem, 32 * cp->part.warps, &pb);
     if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
     if (pb < 1) return GMINE_E_LIMIT;
-    L->part_ctas = (part_global ? std::min(pb, 4) : pb) * dev.sms;
+    cp->part_ctas = (part_global ? std::min(pb, 4) : pb) * dev.sms;
   }
   // the sort: in shared memory up to kMaxRankN samples, else keys and indices
   // in global scratch, two resident CTAs per SM looping over the slots
   {
     int64_t N2 = 1;
     while (N2 < n) N2 <<= 1;
-    L->rank_smem_bytes = rank_smem(n);
-    L->rank_ctas = 0;
-    L->rank_scr_per_cta = 0;
-    if (L->rank_smem_bytes > dev.smem_optin) {
-      L->rank_smem_bytes = 4 * (kRankThreads + 1) + 64;
-      L->rank_ctas = 2 * dev.sms;
-      L->rank_scr_per_cta = (N2 * 12 + 255) & ~int64_t(255);
+    cp->rank_smem_bytes = rank_smem(n);
+    cp->rank_ctas = 0;
+    cp->rank_scr_per_cta = 0;
+    if (cp->rank_smem_bytes > dev.smem_optin) {
+      cp->rank_smem_bytes = 4 * (kRankThreads + 1) + 64;
+      cp->rank_ctas = 2 * dev.sms;
+      cp->rank_scr_per_cta = (N2 * 12 + 255) & ~int64_t(255);
     }
   }
-  L->rec_per_orient = std::max<int64_t>(rec_offset(B, (int)n, param->c, B / 2 + 1), 4);
-  const int64_t rec_pair = 2 * L->rec_per_orient * 4;
+  cp->rec_per_orient = std::max<int64_t>(rec_offset(B, (int)n, c, B / 2 + 1), 4);
+  cp->cells = std::max<int64_t>(host_cells(B), 1);
+  cp->R = std::max(cp->tb.R, 1);
+  cp->bstride = cp->tb.R + 2;
+  return rc;
+}
+
+int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
+                int32_t flags, Layout* L) {
+  if (!param) return GMINE_E_ARG;
+  if (gmine_check_param(param) != GMINE_OK) return GMINE_E_PARAM;
+  if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
+  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
+  if (n > kMaxN) return GMINE_E_LIMIT;
+  DeviceInfo dev;
+  int rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  *L = Layout{};
+  L->n = n;
+  L->p = p;
+  L->n_pairs = n_pairs;
+  const int B = n > 0 ? host_B(n, param->alpha) : 0;
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  rc = plan_chunk(n, B, param->c, fp32, dev, &L->cp);
+  if (rc != GMINE_OK) return rc;
+  const int64_t rec_pair = 2 * L->cp.rec_per_orient * 4;
   L->chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n_pairs, kChunkPairs),
                                                     kRecBudget / rec_pair));
   L->slots = p + 2 * L->chunk;
-  L->cells_max = std::max<int64_t>(host_cells(B), 1);
 
   const int64_t S = L->slots;
-  const int R = std::max(L->tb.R, 1);
-  const int bstride = L->tb.R + 2;
+  const int R = L->cp.R;
+  const int bstride = L->cp.bstride;
   int64_t o = 0;
   auto take = [&](int64_t bytes) {
     const int64_t at = o;
     o = align256(o + std::max<int64_t>(bytes, 1));
     return at;
   };
-  L->o_partscr = part_global ? take((int64_t)L->part_ctas * ((L->part.total + 255) & ~255)) : -1;
-  L->o_rankscr = L->rank_ctas > 0 ? take((int64_t)L->rank_ctas * L->rank_scr_per_cta) : -1;
-  L->o_Btab = take(4 * (n + 1));
+  L->partscr_bytes = L->cp.part_global ? (int64_t)L->cp.part_ctas * ((L->cp.part.total + 255) & ~255) : 0;
+  L->o_partscr = L->cp.part_global ? take(L->partscr_bytes) : -1;
+  L->rankscr_bytes = L->cp.rank_ctas > 0 ? (int64_t)L->cp.rank_ctas * L->cp.rank_scr_per_cta : 0;
+  L->o_rankscr = L->cp.rank_ctas > 0 ? take(L->rankscr_bytes) : -1;
+  L->n_tables = 2;
+  L->o_Btab = take(4 * (n + 1) * L->n_tables);
   L->o_L64 = take(8 * (n + 1));
   L->o_L32 = take(4 * (n + 1));
   L->o_lnt = take(8 * (n + 1));
-  L->o_recoff = take(8 * (B / 2 + 2));
+  L->o_recoff = take(8 * (L->cp.B / 2 + 2));
   L->o_nf = take(4 * p);
   L->o_perm = take(4 * S * n);
   L->o_pos = take(4 * S * n);
@@ -607,15 +659,15 @@ int make_layout(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param,
   L->o_dirty = take(4 * L->chunk);
   L->o_ndirty = take(4);
   L->o_rec = take(L->chunk * rec_pair);
-  L->o_Mo = take(8 * L->chunk * 2 * L->cells_max);
+  L->o_Mo = take(8 * L->chunk * 2 * L->cp.cells);
   L->o_queue = take(8 * (kMaxDPGroups + 1));
-  for (int gi = 0; gi < L->ngroups; ++gi)
-    L->grp[gi].o_scratch = take(L->grp[gi].scratch_per_cta * L->grp[gi].ctas);
+  for (int gi = 0; gi < L->cp.ngroups; ++gi)
+    L->cp.grp[gi].o_scratch = take(L->cp.grp[gi].scratch_per_cta * L->cp.grp[gi].ctas);
   if (flags & GMINE_PLAN_HOST_STAGING) {
     L->o_hvars = take(8 * p * n);
     L->o_hpairs = take(4 * 2 * n_pairs);
     L->o_hscores = take((int64_t)sizeof(gmine_pair_score) * n_pairs);
-    L->o_hM = take(8 * n_pairs * L->cells_max);
+    L->o_hM = take(8 * n_pairs * L->cp.cells);
   } else {
     L->o_hvars = L->o_hpairs = L->o_hscores = L->o_hM = -1;
   }
@@ -644,19 +696,24 @@ EquiData equi_data(void* ws, const Layout& L) {
   EquiData eq;
   eq.bounds = at<int32_t>(ws, L.o_bounds);
   eq.yhat = at<int32_t>(ws, L.o_yhat);
-  eq.R = std::max(L.tb.R, 1);
-  eq.bstride = L.tb.R + 2;
+  eq.R = L.cp.R;
+  eq.bstride = L.cp.bstride;
   return eq;
 }
 
 PairPrep pair_prep(void* ws, const Layout& L) {
-  PairPrep pp;
+  PairPrep pp{};
   pp.slot = at<int32_t>(ws, L.o_slot);
   pp.n_used = at<int32_t>(ws, L.o_nused);
   pp.B = at<int32_t>(ws, L.o_Bp);
   pp.flags = at<int32_t>(ws, L.o_flags);
   pp.dirty = at<int32_t>(ws, L.o_dirty);
   pp.ndirty = at<int32_t>(ws, L.o_ndirty);
+  pp.order = nullptr;
+  pp.aidx = nullptr;
+  pp.btab_stride = L.n + 1;
+  pp.slot0 = L.uneven ? 0 : L.p;
+  pp.all_dirty = L.uneven ? 1 : 0;
   return pp;
 }
 
@@ -666,15 +723,23 @@ int rank_smem(int64_t n) {
   return (int)(N2 * 12 + 4 * (kRankThreads + 1) + 64);
 }
 
-// B(m) = floor(m^alpha) for m = 0..n, written into the workspace.
-int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
-  // one host buffer per thread, grown to the largest n seen (no device
+// B(m) = floor(m^alpha) for m = 0..n, one table per alpha and then one for
+// the largest alpha, written into the workspace.
+int upload_Btab(void* ws, const Layout& L, const double* alphas, int na, cudaStream_t st) {
+  // one host buffer per thread, grown to the largest size seen (no device
   // allocation); the copy from pageable memory returns once the data is
   // staged, so the buffer can be reused at once
   static thread_local std::vector<int32_t> Bt;
-  if ((int64_t)Bt.size() < L.n + 1) Bt.resize((size_t)L.n + 1);
-  for (int64_t m = 0; m <= L.n; ++m) Bt[m] = m > 0 ? host_B(m, alpha) : 0;
-  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt.data(), sizeof(int32_t) * (size_t)(L.n + 1),
+  const int64_t stride = L.n + 1;
+  const size_t need = (size_t)(stride * (na + 1));
+  if (Bt.size() < need) Bt.resize(need);
+  double amax = alphas[0];
+  for (int a = 1; a < na; ++a) amax = std::max(amax, alphas[a]);
+  for (int a = 0; a <= na; ++a) {
+    const double al = a < na ? alphas[a] : amax;
+    for (int64_t m = 0; m <= L.n; ++m) Bt[(size_t)(a * stride + m)] = m > 0 ? host_B(m, al) : 0;
+  }
+  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_Btab), Bt.data(), sizeof(int32_t) * need,
                           cudaMemcpyHostToDevice, st));
   return GMINE_OK;
 }
@@ -682,11 +747,11 @@ int upload_Btab(void* ws, const Layout& L, double alpha, cudaStream_t st) {
 // Ranks and equipartitions of the clean variables (slots 0..p-1).
 int prepare_variables(const double* d_vars, void* ws, const Layout& L, double alpha, double c,
                       cudaStream_t st, int* launches) {
-  int rc = upload_Btab(ws, L, alpha, st);
+  int rc = upload_Btab(ws, L, &alpha, 1, st);
   if (rc != GMINE_OK) return rc;
   const int n = (int)L.n;
-  k_tables<<<(std::max(n, L.B) + 256) / 256, 256, 0, st>>>(
-      n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32), at<double>(ws, L.o_lnt), L.B, c,
+  k_tables<<<(std::max(n, L.cp.B) + 256) / 256, 256, 0, st>>>(
+      n, at<double>(ws, L.o_L64), at<float>(ws, L.o_L32), at<double>(ws, L.o_lnt), L.cp.B, n, c,
       at<int64_t>(ws, L.o_recoff));
   GM_CUDA(cudaGetLastError());
   ++*launches;
@@ -694,16 +759,16 @@ int prepare_variables(const double* d_vars, void* ws, const Layout& L, double al
     k_nonfinite<<<(unsigned)((L.p + 7) / 8), 256, 0, st>>>(d_vars, L.p, n, at<int32_t>(ws, L.o_nf));
     GM_CUDA(cudaGetLastError());
     ++*launches;
-    const int smem = L.rank_smem_bytes;
+    const int smem = L.cp.rank_smem_bytes;
     PairPrep pp = pair_prep(ws, L);
     unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
-    const int64_t rgrid = rscr ? std::min<int64_t>(L.p, L.rank_ctas) : L.p;
-    GM_CUDA(rank_launch((int)rgrid, kRankThreads, smem, st, d_vars, L.p, n,
-                        at<int32_t>(ws, L.o_nf), nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0, L.p,
-                        rank_data(ws, L), rscr, L.rank_scr_per_cta));
+    const int64_t rgrid = rscr ? std::min<int64_t>(L.p, L.cp.rank_ctas) : L.p;
+    GM_CUDA(rank_launch((int)rgrid, kRankThreads, smem, st, d_vars, n, n, at<int32_t>(ws, L.o_nf),
+                        nullptr, 0, pp, at<int32_t>(ws, L.o_Btab), 0, L.p, rank_data(ws, L), rscr,
+                        L.cp.rank_scr_per_cta));
     ++*launches;
-    if (L.tb.R > 0) {
-      const int64_t work = L.p * L.tb.R;
+    if (L.cp.tb.R > 0) {
+      const int64_t work = L.p * L.cp.tb.R;
       k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
           0, L.p, L.p, at<int32_t>(ws, L.o_Btab), nullptr, rank_data(ws, L), equi_data(ws, L));
       GM_CUDA(cudaGetLastError());
@@ -715,10 +780,401 @@ int prepare_variables(const double* d_vars, void* ws, const Layout& L, double al
 
 bool plausible_device_ptr(const void* p) { return p != nullptr; }
 
+// Working memory of one chunk of pairs (device pointers).
+struct ChunkMem {
+  RankData rk;
+  EquiData eq;
+  PairPrep pp;
+  int32_t* rec;
+  double* Mo;
+  int64_t* rec_off;
+  unsigned long long* queue;  // [kMaxDPGroups + 1]
+  unsigned char* partscr;     // partition regions in global memory, if planned
+  int64_t partscr_bytes;
+  unsigned char* rankscr;     // sort keys in global memory, if planned
+  int64_t rankscr_bytes;
+  char* dpscr;                // one region for every DP group (NULL: each group's own)
+  int64_t dpscr_bytes;
+};
+
+ChunkMem regular_mem(void* ws, const Layout& L) {
+  ChunkMem cm{};
+  cm.rk = rank_data(ws, L);
+  cm.eq = equi_data(ws, L);
+  cm.pp = pair_prep(ws, L);
+  cm.rec = at<int32_t>(ws, L.o_rec);
+  cm.Mo = at<double>(ws, L.o_Mo);
+  cm.rec_off = at<int64_t>(ws, L.o_recoff);
+  cm.queue = at<unsigned long long>(ws, L.o_queue);
+  cm.partscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
+  cm.partscr_bytes = L.partscr_bytes;
+  cm.rankscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
+  cm.rankscr_bytes = L.rankscr_bytes;
+  cm.dpscr = nullptr;
+  cm.dpscr_bytes = 0;
+  return cm;
+}
+
+// Everything one batch call shares across its chunks.
+struct BatchCtx {
+  const double* vars;
+  int64_t p, n_row;
+  const int32_t* pairs;
+  int64_t n_pairs;
+  double c;
+  bool fp32;
+  void* ws;
+  const Layout* L;
+  const int32_t* Btab;        // the pairs' B tables
+  const int32_t* Btab_slots;  // the table of the largest alpha (slots)
+  const int32_t* nf;          // non-finite samples per variable (regular batches)
+  gmine_pair_score* scores;
+  double* M;
+  int64_t m_stride;
+  const gmine_trace* trace;
+  DPTiming* timing;
+  cudaStream_t st;
+  int launches;
+};
+
+// One chunk: pairs at batch positions [pair0, pair0 + C), planned by cp:
+// pair slots, their own ranks and equipartitions where needed, the
+// partitions of every task, the DP launches, M and the statistics.
+int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair0, int64_t C) {
+  const Layout& L = *b.L;
+  cudaStream_t st = b.st;
+  PairPrep pp = cm.pp;
+  GM_CUDA(cudaMemsetAsync(pp.ndirty, 0, 4, st));
+  k_pair_prep<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(b.pairs, pair0, C, b.p, (int)b.n_row,
+                                                            b.nf, b.Btab, pp);
+  GM_CUDA(cudaGetLastError());
+  ++b.launches;
+  {
+    // pairs with their own (compacted) ranks
+    unsigned char* rscr = nullptr;
+    int64_t rctas = 0;
+    if (cp.rank_ctas > 0) {
+      rscr = cm.rankscr;
+      rctas = std::min<int64_t>(cp.rank_ctas, cm.rankscr_bytes / std::max<int64_t>(cp.rank_scr_per_cta, 1));
+      if (!rscr || rctas < 1) return GMINE_E_WORKSPACE;
+    }
+    const int64_t rgrid = rscr ? std::min<int64_t>(2 * C, rctas) : 2 * C;
+    GM_CUDA(rank_launch((int)rgrid, kRankThreads, cp.rank_smem_bytes, st, b.vars, b.n_row, (int)cp.n,
+                        b.nf, b.pairs, pair0, pp, b.Btab, pp.slot0, 2 * C, cm.rk, rscr,
+                        cp.rank_scr_per_cta));
+    ++b.launches;
+  }
+  if (cp.tb.R > 0) {
+    const int64_t work = 2 * C * cp.tb.R;
+    k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(pp.slot0, 2 * C, pp.slot0, b.Btab_slots,
+                                                           pp.ndirty, cm.rk, cm.eq);
+    GM_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
+  const int64_t ntasks = 2 * (int64_t)cp.tb.R * C;
+  if (ntasks > 0) {
+    // partition of every task of the chunk
+    PartParams Q{};
+    Q.rk = cm.rk;
+    Q.eq = cm.eq;
+    Q.pp = pp;
+    Q.L64 = at<double>(b.ws, L.o_L64);
+    Q.lnt = at<double>(b.ws, L.o_lnt);
+    Q.rec = cm.rec;
+    Q.rec_per_orient = cp.rec_per_orient;
+    Q.rec_off = cm.rec_off;
+    Q.B_full = cp.B;
+    Q.n_full = (int)cp.n;
+    Q.c = b.c;
+    Q.chunk_pairs = C;
+    Q.queue = cm.queue + kMaxDPGroups;
+    Q.off_pi = cp.part.off_pi;
+    Q.off_gU = cp.part.off_gU;
+    Q.off_warps = cp.part.off_warps;
+    Q.warp_smem = cp.part.warp_smem;
+    Q.off_Qs = cp.part.off_Qs;
+    Q.off_q = cp.part.off_q;
+    Q.off_cgrp = cp.part.off_cgrp;
+    Q.off_cstart = cp.part.off_cstart;
+    Q.off_scb = cp.part.off_scb;
+    Q.off_mixed = cp.part.off_mixed;
+    Q.off_eb = cp.part.off_eb;
+    Q.gscr_per_cta = (cp.part.total + 255) & ~255;
+    int pctas = cp.part_ctas;
+    Q.gscr = nullptr;
+    if (cp.part_global) {
+      Q.gscr = cm.partscr;
+      pctas = (int)std::min<int64_t>(pctas, cm.partscr_bytes / Q.gscr_per_cta);
+      if (!Q.gscr || pctas < 1) return GMINE_E_WORKSPACE;
+    }
+    GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
+    GM_CUDA(partition_launch(cp.part_global, cp.part_wide, pctas, 32 * cp.part.warps,
+                             cp.part_global ? 0 : cp.part.total, st, Q));
+    GM_CUDA(cudaGetLastError());
+    ++b.launches;
+    // the dynamic program: large row counts... small row counts
+    DPParams P{};
+    P.pp = pp;
+    P.rec = Q.rec;
+    P.rec_per_orient = cp.rec_per_orient;
+    P.rec_off = Q.rec_off;
+    P.B_full = cp.B;
+    P.n_full = (int)cp.n;
+    P.c = b.c;
+    P.L64 = at<double>(b.ws, L.o_L64);
+    P.L32 = at<float>(b.ws, L.o_L32);
+    P.lnt = at<double>(b.ws, L.o_lnt);
+    P.Mo = cm.Mo;
+    P.cells_max = (int)cp.cells;
+    P.chunk_pairs = C;
+    P.counters = b.trace ? b.trace->d_counters : nullptr;
+    if (b.trace) P.trace = *b.trace;
+    P.trace_pair0 = pair0;
+    P.trace_npairs = b.n_pairs;
+    unsigned long long* qs = cm.queue;
+    GM_CUDA(cudaMemsetAsync(qs, 0, 8 * kMaxDPGroups, st));
+    for (int gi = 0; gi < cp.ngroups; ++gi) {
+      const DPGroup& g = cp.grp[gi];
+      P.task_begin = 2 * (int64_t)(g.ylo - 2) * C;
+      P.task_end = 2 * (int64_t)(g.yhi - 1) * C;
+      P.queue = qs + gi;
+      P.scratch_per_cta = g.scratch_per_cta;
+      int ctas = g.ctas;
+      if (cm.dpscr) {
+        P.scratch = cm.dpscr;
+        if (g.scratch_per_cta > 0) {
+          ctas = (int)std::min<int64_t>(ctas, cm.dpscr_bytes / g.scratch_per_cta);
+          if (ctas < 1) return GMINE_E_WORKSPACE;
+        }
+      } else {
+        P.scratch = at<char>(b.ws, g.o_scratch);
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (b.timing) {
+        GM_CUDA(b.timing->pair(&e0, &e1));
+        GM_CUDA(cudaEventRecord(e0, st));
+      }
+      if (g.two)
+        GM_CUDA(dp_two_launch(b.fp32, ctas, g.threads, g.smem_two, st, P, g.off_two_rec,
+                              g.two_rec_bytes));
+      else if (g.warp)
+        GM_CUDA(dp_warp_launch(g.lev, g.tdw, ctas, g.threads, g.WS.total, st, P, g.WS));
+      else if (g.mid)
+        GM_CUDA(dp_mid_launch(b.fp32, ctas, g.threads, g.MS.total, st, P, g.MS));
+      else if (g.small)
+        GM_CUDA(dp_small_launch(b.fp32, ctas, g.threads, g.SS.total, st, P, g.SS));
+      else
+        GM_CUDA(dp_launch(b.fp32, g.rsm, g.lev, ctas, g.threads, g.S.total, st, P, g.S));
+      ++b.launches;
+      if (b.timing) GM_CUDA(cudaEventRecord(e1, st));
+    }
+  }
+  FinalParams F{};
+  F.Mo = cm.Mo;
+  F.cells_max = (int)cp.cells;
+  F.pp = pp;
+  F.chunk_pairs = C;
+  F.pair0 = pair0;
+  F.scores = b.scores;
+  F.M = b.M;
+  F.m_stride = b.m_stride;
+  F.eq_yhat = cm.eq.yhat;
+  F.R = cm.eq.R;
+  k_final<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(F);
+  GM_CUDA(cudaGetLastError());
+  ++b.launches;
+  return GMINE_OK;
+}
+
+// The trace epilogue of a batch call: launch count and DP kernel time.
+int finish_trace(const BatchCtx& b) {
+  if (b.trace && b.trace->h_kernel_launches) *b.trace->h_kernel_launches = b.launches;
+  if (b.timing) {
+    GM_CUDA(cudaStreamSynchronize(b.st));
+    double ms = 0.0;
+    GM_CUDA(b.timing->total_ms(&ms));
+    *b.trace->h_dp_ms = ms;
+    if (b.trace->h_dp_launches) *b.trace->h_dp_launches = b.timing->launches();
+  }
+  return GMINE_OK;
+}
+
+// ---- uneven batches --------------------------------------------------------
+
+constexpr int kMaxAlphas = 8;
+constexpr int64_t kUnevenRankBudget = 2LL << 30;   // per-slot rank arrays of a chunk
+constexpr int64_t kUnevenEquiBudget = 2LL << 30;   // equipartitions of a chunk
+constexpr int64_t kUnevenRecBudget = 24LL << 30;   // task records of a chunk
+constexpr int64_t kUnevenMoBudget = 1LL << 30;     // M of both orientations of a chunk
+
+// Bytes a chunk of C pairs with at most n samples and B <= Bc needs in each
+// region of the uneven layout (sub-arrays 256-byte aligned).
+struct ChunkBytes {
+  int64_t rank, equi, rec, Mo;
+};
+
+ChunkBytes chunk_bytes(int64_t C, int64_t n, int B, double c) {
+  ChunkBytes cb{};
+  const int64_t S = 2 * C;
+  cb.rank = 3 * align256(4 * S * n) + align256(4 * S * (n + 1)) + 2 * align256(4 * S);
+  const int64_t R = std::max(B / 2 - 1, 1);
+  cb.equi = align256(4 * S * R * (R + 2)) + align256(4 * S * R);
+  cb.rec = S * std::max<int64_t>(rec_offset(B, (int)n, c, B / 2 + 1), 4) * 4;
+  cb.Mo = 8 * S * std::max<int64_t>(host_cells(B), 1);
+  return cb;
+}
+
+int check_alphas(const double* alphas, int na, double c) {
+  if (!alphas || na < 1) return GMINE_E_ARG;
+  if (na > kMaxAlphas) return GMINE_E_LIMIT;
+  for (int a = 0; a < na; ++a) {
+    const gmine_param prm{alphas[a], c};
+    if (gmine_check_param(&prm) != GMINE_OK) return GMINE_E_PARAM;
+  }
+  return GMINE_OK;
+}
+
+int make_layout_uneven(int64_t p, int64_t n, int64_t n_pairs, const double* alphas, int na,
+                       double c, int32_t precision, Layout* L) {
+  int rc = check_alphas(alphas, na, c);
+  if (rc != GMINE_OK) return rc;
+  if (p < 0 || n < 0 || n_pairs < 0) return GMINE_E_ARG;
+  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
+  if (n > kMaxN) return GMINE_E_LIMIT;
+  DeviceInfo dev;
+  rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  *L = Layout{};
+  L->uneven = true;
+  L->n = n;
+  L->p = p;
+  L->n_pairs = n_pairs;
+  double amax = alphas[0];
+  for (int a = 1; a < na; ++a) amax = std::max(amax, alphas[a]);
+  const int B = n > 0 ? host_B(n, amax) : 0;
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  // the largest chunk plan bounds the scratch regions; the others fit them
+  // with fewer CTAs at most
+  rc = plan_chunk(std::max<int64_t>(n, 4), B, c, fp32, dev, &L->cp);
+  if (rc != GMINE_OK) return rc;
+  L->chunk = std::max<int64_t>(1, std::min<int64_t>(n_pairs, kChunkPairs));
+  L->n_tables = na + 1;
+  const ChunkBytes one = chunk_bytes(1, std::max<int64_t>(n, 4), B, c);
+  const ChunkBytes all = chunk_bytes(std::max<int64_t>(L->chunk, 1), std::max<int64_t>(n, 4), B, c);
+  auto cap = [](int64_t one_pair, int64_t all_pairs, int64_t budget) {
+    return std::max(one_pair, std::min(all_pairs, budget));
+  };
+  L->rank_bytes = cap(one.rank, all.rank, kUnevenRankBudget);
+  L->equi_bytes = cap(one.equi, all.equi, kUnevenEquiBudget);
+  L->rec_bytes = cap(one.rec, all.rec, kUnevenRecBudget);
+  L->Mo_bytes = cap(one.Mo, all.Mo, kUnevenMoBudget);
+  int64_t dps = 0;
+  for (int gi = 0; gi < L->cp.ngroups; ++gi)
+    dps = std::max(dps, L->cp.grp[gi].scratch_per_cta * L->cp.grp[gi].ctas);
+  L->dpscr_bytes = dps;
+  int64_t o = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t at = o;
+    o = align256(o + std::max<int64_t>(bytes, 1));
+    return at;
+  };
+  L->partscr_bytes = L->cp.part_global ? (int64_t)L->cp.part_ctas * ((L->cp.part.total + 255) & ~255) : 0;
+  L->o_partscr = L->cp.part_global ? take(L->partscr_bytes) : -1;
+  L->rankscr_bytes = L->cp.rank_ctas > 0 ? (int64_t)L->cp.rank_ctas * L->cp.rank_scr_per_cta : 0;
+  L->o_rankscr = L->cp.rank_ctas > 0 ? take(L->rankscr_bytes) : -1;
+  L->o_Btab = take(4 * (n + 1) * L->n_tables);
+  L->o_L64 = take(8 * (n + 1));
+  L->o_L32 = take(4 * (n + 1));
+  L->o_lnt = take(8 * (n + 1));
+  L->o_recoff = take(8 * (B / 2 + 2));
+  L->o_rank = take(L->rank_bytes);
+  L->o_equi = take(L->equi_bytes);
+  L->o_slot = take(4 * 2 * L->chunk);
+  L->o_nused = take(4 * L->chunk);
+  L->o_Bp = take(4 * L->chunk);
+  L->o_flags = take(4 * L->chunk);
+  L->o_dirty = take(4 * L->chunk);
+  L->o_ndirty = take(4);
+  L->o_rec = take(L->rec_bytes);
+  L->o_Mo = take(L->Mo_bytes);
+  L->o_queue = take(8 * (kMaxDPGroups + 1));
+  L->o_dpscr = take(L->dpscr_bytes);
+  L->o_count = take(8 * n_pairs);
+  L->o_order = take(4 * n_pairs);
+  L->o_nf = L->o_perm = L->o_pos = L->o_grp = L->o_gstart = L->o_ngroups = L->o_nslot = -1;
+  L->o_bounds = L->o_yhat = -1;
+  L->o_hvars = L->o_hpairs = L->o_hscores = L->o_hM = -1;
+  L->total = o;
+  return GMINE_OK;
+}
+
+// Relative DP work of a pair with n samples and this B: per row count y the
+// recursion over k <= min(c x, n) superclumps for x = floor(B / y) columns,
+// both orientations alike (the sort key of the chunk planner).
+double pair_cost(int n, int B, double c) {
+  if (n < 4 || B < 4) return 0.0;
+  double w = 0.0;
+  for (int y = 2; y <= B / 2; ++y) {
+    const double x = B / y;
+    const double k = std::min<double>(host_khat(B, y, c), n);
+    w += (x - 1.0) * k * k * 0.5 + k * k * 0.5 * y;
+  }
+  return w;
+}
+
+// The chunk's working arrays inside the uneven layout's regions, for C pairs
+// of at most n samples and B <= Bc.
+ChunkMem uneven_mem(void* ws, const Layout& L, int64_t C, int64_t n, int B) {
+  ChunkMem cm{};
+  const int64_t S = 2 * C;
+  int64_t o = L.o_rank;
+  auto sub = [&](int64_t bytes) { const int64_t at = o; o += align256(bytes); return at; };
+  cm.rk.perm = at<int32_t>(ws, sub(4 * S * n));
+  cm.rk.pos = at<int32_t>(ws, sub(4 * S * n));
+  cm.rk.grp = at<int32_t>(ws, sub(4 * S * n));
+  cm.rk.gstart = at<int32_t>(ws, sub(4 * S * (n + 1)));
+  cm.rk.ngroups = at<int32_t>(ws, sub(4 * S));
+  cm.rk.nslot = at<int32_t>(ws, sub(4 * S));
+  cm.rk.stride = n;
+  const int R = std::max(B / 2 - 1, 1);
+  o = L.o_equi;
+  cm.eq.bounds = at<int32_t>(ws, sub(4 * S * (int64_t)R * (R + 2)));
+  cm.eq.yhat = at<int32_t>(ws, sub(4 * S * (int64_t)R));
+  cm.eq.R = R;
+  cm.eq.bstride = std::max(B / 2 - 1, 0) + 2;
+  cm.pp = pair_prep(ws, L);
+  cm.pp.order = at<int32_t>(ws, L.o_order);
+  cm.rec = at<int32_t>(ws, L.o_rec);
+  cm.Mo = at<double>(ws, L.o_Mo);
+  cm.rec_off = at<int64_t>(ws, L.o_recoff);
+  cm.queue = at<unsigned long long>(ws, L.o_queue);
+  cm.partscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
+  cm.partscr_bytes = L.partscr_bytes;
+  cm.rankscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
+  cm.rankscr_bytes = L.rankscr_bytes;
+  cm.dpscr = at<char>(ws, L.o_dpscr);
+  cm.dpscr_bytes = L.dpscr_bytes;
+  return cm;
+}
+
 }  // namespace
 
 namespace gm {
 void note_cuda_error(cudaError_t e) { last_cuda_error() = e; }
+
+cudaError_t allow_dynamic_smem(const void* func, int smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& have = granted[{func, dev}];
+  if (smem <= have) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) have = smem;
+  return e;
+}
 }  // namespace gm
 
 extern "C" {
@@ -757,7 +1213,7 @@ int gmine_plan(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, 
   Layout L;
   const int rc = make_layout(p, n, n_pairs, param, precision, flags, &L);
   if (rc != GMINE_OK) return rc;
-  if (m_cells_per_pair) *m_cells_per_pair = L.cells_max;
+  if (m_cells_per_pair) *m_cells_per_pair = L.cp.cells;
   if (workspace_bytes) *workspace_bytes = L.total;
   return GMINE_OK;
 }
@@ -779,144 +1235,34 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   int launches = 0;
   rc = prepare_variables(d_vars, ws, L, param->alpha, param->c, st, &launches);
   if (rc != GMINE_OK) return rc;
-
-  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
-  const int rsmem = L.rank_smem_bytes;
   if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
   DPTiming tim;
-  DPTiming* timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
+  BatchCtx b{};
+  b.vars = d_vars;
+  b.p = p;
+  b.n_row = n;
+  b.pairs = d_pairs;
+  b.n_pairs = n_pairs;
+  b.c = param->c;
+  b.fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  b.ws = ws;
+  b.L = &L;
+  b.Btab = at<int32_t>(ws, L.o_Btab);
+  b.Btab_slots = b.Btab;
+  b.nf = at<int32_t>(ws, L.o_nf);
+  b.scores = d_scores;
+  b.M = d_M;
+  b.m_stride = L.cp.cells;
+  b.trace = trace;
+  b.timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
+  b.st = st;
+  b.launches = launches;
+  const ChunkMem cm = regular_mem(ws, L);
   for (int64_t pair0 = 0; pair0 < n_pairs; pair0 += L.chunk) {
-    const int64_t C = std::min(L.chunk, n_pairs - pair0);
-    PairPrep pp = pair_prep(ws, L);
-    GM_CUDA(cudaMemsetAsync(pp.ndirty, 0, 4, st));
-    k_pair_prep<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
-        d_pairs, pair0, C, L.p, (int)L.n, at<int32_t>(ws, L.o_nf), at<int32_t>(ws, L.o_Btab), pp);
-    GM_CUDA(cudaGetLastError());
-    ++launches;
-    // pairs with missing samples: compacted per-pair ranks and equipartitions
-    {
-      unsigned char* rscr = L.o_rankscr >= 0 ? at<unsigned char>(ws, L.o_rankscr) : nullptr;
-      const int64_t rgrid = rscr ? std::min<int64_t>(2 * C, L.rank_ctas) : 2 * C;
-      GM_CUDA(rank_launch((int)rgrid, kRankThreads, rsmem, st, d_vars, L.p, (int)L.n,
-                          at<int32_t>(ws, L.o_nf), d_pairs, pair0, pp, at<int32_t>(ws, L.o_Btab),
-                          L.p, 2 * C, rank_data(ws, L), rscr, L.rank_scr_per_cta));
-    }
-    ++launches;
-    if (L.tb.R > 0) {
-      const int64_t work = 2 * C * L.tb.R;
-      k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
-          L.p, 2 * C, L.p, at<int32_t>(ws, L.o_Btab), pp.ndirty, rank_data(ws, L),
-          equi_data(ws, L));
-      GM_CUDA(cudaGetLastError());
-      ++launches;
-    }
-    // partition of every task of the chunk
-    const int64_t ntasks = 2 * (int64_t)L.tb.R * C;
-    if (ntasks > 0) {
-      PartParams Q{};
-      Q.rk = rank_data(ws, L);
-      Q.eq = equi_data(ws, L);
-      Q.pp = pp;
-      Q.L64 = at<double>(ws, L.o_L64);
-      Q.lnt = at<double>(ws, L.o_lnt);
-      Q.rec = at<int32_t>(ws, L.o_rec);
-      Q.rec_per_orient = L.rec_per_orient;
-      Q.rec_off = at<int64_t>(ws, L.o_recoff);
-      Q.B_full = L.B;
-      Q.n_full = (int)L.n;
-      Q.c = param->c;
-      Q.chunk_pairs = C;
-      Q.queue = at<unsigned long long>(ws, L.o_queue) + kMaxDPGroups;
-      Q.off_pi = L.part.off_pi;
-      Q.off_gU = L.part.off_gU;
-      Q.off_warps = L.part.off_warps;
-      Q.warp_smem = L.part.warp_smem;
-      Q.off_Qs = L.part.off_Qs;
-      Q.off_q = L.part.off_q;
-      Q.off_cgrp = L.part.off_cgrp;
-      Q.off_cstart = L.part.off_cstart;
-      Q.off_scb = L.part.off_scb;
-      Q.off_mixed = L.part.off_mixed;
-      Q.off_eb = L.part.off_eb;
-      Q.gscr = L.o_partscr >= 0 ? at<unsigned char>(ws, L.o_partscr) : nullptr;
-      Q.gscr_per_cta = (L.part.total + 255) & ~255;
-      GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
-      GM_CUDA(partition_launch(Q.gscr != nullptr, L.part_wide, L.part_ctas, 32 * L.part.warps,
-                               Q.gscr ? 0 : L.part.total, st, Q));
-      GM_CUDA(cudaGetLastError());
-      ++launches;
-      // the dynamic program: large row counts... small row counts
-      DPParams P{};
-      P.pp = pp;
-      P.rec = Q.rec;
-      P.rec_per_orient = L.rec_per_orient;
-      P.rec_off = Q.rec_off;
-      P.B_full = L.B;
-      P.n_full = (int)L.n;
-      P.c = param->c;
-      P.L64 = at<double>(ws, L.o_L64);
-      P.L32 = at<float>(ws, L.o_L32);
-      P.lnt = at<double>(ws, L.o_lnt);
-      P.Mo = at<double>(ws, L.o_Mo);
-      P.cells_max = (int)L.cells_max;
-      P.chunk_pairs = C;
-      P.counters = trace ? trace->d_counters : nullptr;
-      if (trace) P.trace = *trace;
-      P.trace_pair0 = pair0;
-      P.trace_npairs = n_pairs;
-      unsigned long long* qs = at<unsigned long long>(ws, L.o_queue);
-      GM_CUDA(cudaMemsetAsync(qs, 0, 8 * kMaxDPGroups, st));
-      for (int gi = 0; gi < L.ngroups; ++gi) {
-        const DPGroup& g = L.grp[gi];
-        P.task_begin = 2 * (int64_t)(g.ylo - 2) * C;
-        P.task_end = 2 * (int64_t)(g.yhi - 1) * C;
-        P.queue = qs + gi;
-        P.scratch = at<char>(ws, g.o_scratch);
-        P.scratch_per_cta = g.scratch_per_cta;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (timing) {
-          GM_CUDA(timing->pair(&e0, &e1));
-          GM_CUDA(cudaEventRecord(e0, st));
-        }
-        if (g.two)
-          GM_CUDA(dp_two_launch(fp32, g.ctas, g.threads, g.smem_two, st, P, g.off_two_rec,
-                                g.two_rec_bytes));
-        else if (g.warp)
-          GM_CUDA(dp_warp_launch(g.lev, g.tdw, g.ctas, g.threads, g.WS.total, st, P, g.WS));
-        else if (g.mid)
-          GM_CUDA(dp_mid_launch(fp32, g.ctas, g.threads, g.MS.total, st, P, g.MS));
-        else if (g.small)
-          GM_CUDA(dp_small_launch(fp32, g.ctas, g.threads, g.SS.total, st, P, g.SS));
-        else
-          GM_CUDA(dp_launch(fp32, g.rsm, g.lev, g.ctas, g.threads, g.S.total, st, P, g.S));
-        ++launches;
-        if (timing) GM_CUDA(cudaEventRecord(e1, st));
-      }
-    }
-    FinalParams F{};
-    F.Mo = at<double>(ws, L.o_Mo);
-    F.cells_max = (int)L.cells_max;
-    F.pp = pp;
-    F.chunk_pairs = C;
-    F.pair0 = pair0;
-    F.scores = d_scores;
-    F.M = d_M;
-    F.m_stride = L.cells_max;
-    F.eq_yhat = equi_data(ws, L).yhat;
-    F.R = equi_data(ws, L).R;
-    k_final<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(F);
-    GM_CUDA(cudaGetLastError());
-    ++launches;
+    rc = run_chunk(b, L.cp, cm, pair0, std::min(L.chunk, n_pairs - pair0));
+    if (rc != GMINE_OK) return rc;
   }
-  if (trace && trace->h_kernel_launches) *trace->h_kernel_launches = launches;
-  if (timing) {
-    GM_CUDA(cudaStreamSynchronize(st));
-    double ms = 0.0;
-    GM_CUDA(timing->total_ms(&ms));
-    *trace->h_dp_ms = ms;
-    if (trace->h_dp_launches) *trace->h_dp_launches = timing->launches();
-  }
-  return GMINE_OK;
+  return finish_trace(b);
 }
 
 int gmine_compute_batch(const double* d_vars, int64_t p, int64_t n, const int32_t* d_pairs,
@@ -925,6 +1271,131 @@ int gmine_compute_batch(const double* d_vars, int64_t p, int64_t n, const int32_
                         double* d_M, void* stream) {
   return gmine_compute_batch_ex(d_vars, p, n, d_pairs, n_pairs, param, precision, d_workspace,
                                 workspace_bytes, d_scores, d_M, nullptr, stream);
+}
+
+int gmine_plan_uneven(int64_t p, int64_t n, int64_t n_pairs, const double* h_alphas,
+                      int32_t n_alphas, double c, int32_t precision, int64_t* m_cells_per_pair,
+                      int64_t* workspace_bytes) {
+  Layout L;
+  const int rc = make_layout_uneven(p, n, n_pairs, h_alphas, n_alphas, c, precision, &L);
+  if (rc != GMINE_OK) return rc;
+  if (m_cells_per_pair) *m_cells_per_pair = L.cp.cells;
+  if (workspace_bytes) *workspace_bytes = L.total;
+  return GMINE_OK;
+}
+
+int gmine_compute_batch_uneven(const double* d_vars, int64_t p, int64_t n, const int32_t* d_pairs,
+                               int64_t n_pairs, const double* h_alphas, int32_t n_alphas,
+                               const uint8_t* d_alpha_idx, double c, int32_t precision,
+                               void* d_workspace, int64_t workspace_bytes,
+                               gmine_pair_score* d_scores, double* d_M, const gmine_trace* trace,
+                               void* stream) {
+  if (n_pairs > 0 && (!plausible_device_ptr(d_vars) || !d_pairs || !d_scores)) return GMINE_E_ARG;
+  if (!d_workspace) return GMINE_E_ARG;
+  if (n_alphas > 1 && !d_alpha_idx) return GMINE_E_ARG;
+  if (trace && (trace->d_k || trace->d_yhat || trace->d_clumps || trace->d_sc_ends ||
+                trace->d_cuts || trace->d_I))
+    return GMINE_E_ARG;  // per-task outputs follow the batch order: not here
+  Layout L;
+  int rc = make_layout_uneven(p, n, n_pairs, h_alphas, n_alphas, c, precision, &L);
+  if (rc != GMINE_OK) return rc;
+  if (workspace_bytes < L.total) return GMINE_E_WORKSPACE;
+  if (n_pairs == 0) return GMINE_OK;
+  DeviceInfo dev;
+  rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = d_workspace;
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  // the pairs' alpha indices are checked on the host before any table is
+  // read through them
+  if (d_alpha_idx) {
+    std::vector<uint8_t> ai((size_t)n_pairs);
+    GM_CUDA(cudaMemcpyAsync(ai.data(), d_alpha_idx, (size_t)n_pairs, cudaMemcpyDeviceToHost, st));
+    GM_CUDA(cudaStreamSynchronize(st));
+    for (uint8_t a : ai)
+      if (a >= n_alphas) return GMINE_E_ARG;
+  }
+  rc = upload_Btab(ws, L, h_alphas, n_alphas, st);
+  if (rc != GMINE_OK) return rc;
+  int launches = 0;
+  const int32_t* Btab = at<int32_t>(ws, L.o_Btab);
+  k_tables<<<(unsigned)((n + 256) / 256), 256, 0, st>>>((int)n, at<double>(ws, L.o_L64),
+                                                        at<float>(ws, L.o_L32), at<double>(ws, L.o_lnt),
+                                                        L.cp.B, (int)n, c, at<int64_t>(ws, L.o_recoff));
+  GM_CUDA(cudaGetLastError());
+  ++launches;
+  // samples used and B of every pair, read back to plan the chunks
+  int32_t* cnt_d = at<int32_t>(ws, L.o_count);
+  k_pair_count<<<(unsigned)((n_pairs + 7) / 8), 256, 0, st>>>(d_vars, p, n, d_pairs, n_pairs,
+                                                              d_alpha_idx, Btab, n + 1, cnt_d);
+  GM_CUDA(cudaGetLastError());
+  ++launches;
+  std::vector<int32_t> cnt((size_t)(2 * n_pairs));
+  GM_CUDA(cudaMemcpyAsync(cnt.data(), cnt_d, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  // heaviest pairs first, so that each chunk holds pairs of similar size
+  std::vector<double> cost((size_t)n_pairs);
+  for (int64_t i = 0; i < n_pairs; ++i) cost[i] = pair_cost(cnt[2 * i], cnt[2 * i + 1], c);
+  std::vector<int32_t> order((size_t)n_pairs);
+  for (int64_t i = 0; i < n_pairs; ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_order), order.data(), sizeof(int32_t) * order.size(),
+                          cudaMemcpyHostToDevice, st));
+  if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
+  DPTiming tim;
+  BatchCtx b{};
+  b.vars = d_vars;
+  b.p = p;
+  b.n_row = n;
+  b.pairs = d_pairs;
+  b.n_pairs = n_pairs;
+  b.c = c;
+  b.fp32 = fp32;
+  b.ws = ws;
+  b.L = &L;
+  b.Btab = Btab;
+  b.Btab_slots = Btab + (int64_t)n_alphas * (n + 1);
+  b.nf = nullptr;
+  b.scores = d_scores;
+  b.M = d_M;
+  b.m_stride = L.cp.cells;
+  b.trace = trace;
+  b.timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
+  b.st = st;
+  b.launches = launches;
+  int64_t i = 0;
+  while (i < n_pairs) {
+    // the longest run of pairs (in cost order) whose chunk fits every region
+    int64_t j = i, nc = 4;
+    int Bc = 0;
+    while (j < n_pairs && j - i < L.chunk) {
+      const int32_t q = order[j];
+      const int64_t n2 = std::max<int64_t>(nc, cnt[2 * q]);
+      const int B2 = std::max(Bc, cnt[2 * q + 1]);
+      const ChunkBytes cb = chunk_bytes(j - i + 1, n2, B2, c);
+      if (cb.rank > L.rank_bytes || cb.equi > L.equi_bytes || cb.rec > L.rec_bytes ||
+          cb.Mo > L.Mo_bytes) {
+        if (j == i) return GMINE_E_LIMIT;
+        break;
+      }
+      nc = n2;
+      Bc = B2;
+      ++j;
+    }
+    ChunkPlan cp;
+    rc = plan_chunk(nc, Bc, c, fp32, dev, &cp);
+    if (rc != GMINE_OK) return rc;
+    ChunkMem cm = uneven_mem(ws, L, j - i, nc, Bc);
+    cm.pp.aidx = d_alpha_idx;
+    k_tables<<<1, 256, 0, st>>>(-1, nullptr, nullptr, nullptr, Bc, (int)nc, c, cm.rec_off);
+    GM_CUDA(cudaGetLastError());
+    ++b.launches;
+    rc = run_chunk(b, cp, cm, i, j - i);
+    if (rc != GMINE_OK) return rc;
+    i = j;
+  }
+  return finish_trace(b);
 }
 
 int gmine_compute_batch_host(const double* h_vars, int64_t p, int64_t n, const int32_t* h_pairs,
@@ -950,7 +1421,7 @@ int gmine_compute_batch_host(const double* h_vars, int64_t p, int64_t n, const i
   if (rc != GMINE_OK) return rc;
   GM_CUDA(cudaMemcpyAsync(h_scores, ds, sizeof(gmine_pair_score) * n_pairs,
                           cudaMemcpyDeviceToHost, st));
-  if (h_M) GM_CUDA(cudaMemcpyAsync(h_M, dM, 8 * n_pairs * L.cells_max, cudaMemcpyDeviceToHost, st));
+  if (h_M) GM_CUDA(cudaMemcpyAsync(h_M, dM, 8 * n_pairs * L.cp.cells, cudaMemcpyDeviceToHost, st));
   GM_CUDA(cudaStreamSynchronize(st));
   return GMINE_OK;
 }
@@ -995,7 +1466,7 @@ int gmine_equipartition(const double* d_vars, int64_t p, int64_t n, int32_t y, i
   eq1.yhat = at<int32_t>(d_workspace, L.o_yhat);
   eq1.R = 1;
   eq1.bstride = y + 1;
-  if ((int64_t)p * (y + 1) > (int64_t)L.slots * std::max(L.tb.R, 1) * (L.tb.R + 2))
+  if ((int64_t)p * (y + 1) > (int64_t)L.slots * L.cp.R * L.cp.bstride)
     return GMINE_E_LIMIT;
   k_equi_single<<<(unsigned)((p + 127) / 128), 128, 0, st>>>(p, y, rank_data(d_workspace, L), eq1);
   GM_CUDA(cudaGetLastError());

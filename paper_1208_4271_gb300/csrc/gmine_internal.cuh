@@ -203,9 +203,24 @@ struct PairPrep {
   int32_t* n_used;   // [chunk]
   int32_t* B;        // [chunk]
   int32_t* flags;    // [chunk] status bits (1 << GMINE_E_*)
-  int32_t* dirty;    // [chunk] chunk-local indices of pairs with missing samples
+  int32_t* dirty;    // [chunk] chunk-local indices of pairs with their own ranks
   int32_t* ndirty;   // [1]
+  const int32_t* order;   // [pairs] batch position -> pair index (NULL: identity)
+  const uint8_t* aidx;    // [pairs] B table of each pair (NULL: table 0)
+  int64_t btab_stride;    // ints per B table (n + 1)
+  int64_t slot0;          // first slot of the pairs with their own ranks
+  int all_dirty;          // every pair gets its own compacted ranks
 };
+
+// Index of the pair at batch position i (pairs may be processed in a
+// planned order), and its B(m) table.
+__device__ __forceinline__ int64_t pair_index(const PairPrep& pp, int64_t i) {
+  return pp.order ? (int64_t)pp.order[i] : i;
+}
+__device__ __forceinline__ const int32_t* btab_of(const int32_t* Btab, const PairPrep& pp,
+                                                  int64_t pair) {
+  return Btab + (pp.aidx ? (int64_t)pp.aidx[pair] * pp.btab_stride : 0);
+}
 
 struct PartParams {
   RankData rk;
@@ -282,7 +297,10 @@ struct MidPlan {
 struct DPPlan {
   int off_R, off_Rtop, off_X, off_Eb, off_rbuf, off_L, off_sd;
   int64_t sd_scr_off;  // off_sd < 0: the superclump rows live in the CTA's global scratch here
-  int off_I_rel, off_lst_rel;  // traceback scratch inside the X region
+  int64_t x_scr_off;   // off_X < 0: the X buffers live in the CTA's global scratch here
+  int off_tb;          // traceback scratch (cuts, I(l), l*(l)): the X region, or its own
+  int64_t scr_bytes;   // global scratch per CTA (0 when the R table is in shared memory)
+  int off_I_rel, off_lst_rel;  // within the traceback scratch
   int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4
   int LX;     // row stride of the X buffers: levels 1..lmax, odd (the lanes'
               // rows then start in distinct shared-memory banks)

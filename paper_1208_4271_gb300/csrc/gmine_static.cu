@@ -9,10 +9,13 @@
 // acceptable.  They still pass their own inputs and outputs; only the
 // scratch memory comes from here.
 //
-// The array is a file-scope __device__ object, so every GPU on which the
-// library uses it keeps its kStaticScratchBytes until the process exits.  On
+// The array is a file-scope __device__ object of this file's module: under
+// lazy module loading (the runtime's default) a GPU reserves its
+// kStaticScratchBytes when this call first runs there, under eager loading
+// whenever the process uses that GPU; it stays until the process exits.  On
 // the first call on a device (with that device current) its device address
-// is looked up with cudaGetSymbolAddress and kept; host code never passes
+// is looked up with cudaGetSymbolAddress and kept (a device reset after that
+// is not supported: the kept address would be stale); host code never passes
 // the array's name itself to a kernel, since in host code that name is only
 // a stand-in for the device object.
 #include <mutex>

@@ -384,7 +384,10 @@ k_dp(DPParams P, DPPlan S) {
   real* Rt = RSM ? reinterpret_cast<real*>(sm + S.off_R)
                  : reinterpret_cast<real*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta);
   real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // R(k, lmax)
-  U* Xb = reinterpret_cast<U*>(sm + S.off_X);             // [2][32][LX] bits
+  // [2][32][LX] bits: shared memory, or (many levels in double) the CTA's
+  // global scratch
+  U* Xb = S.off_X >= 0 ? reinterpret_cast<U*>(sm + S.off_X)
+                       : reinterpret_cast<U*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.x_scr_off);
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);  // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
@@ -392,9 +395,10 @@ k_dp(DPParams P, DPPlan S) {
   int* sd = (!RSM && S.off_sd < 0)
                 ? reinterpret_cast<int*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.sd_scr_off)
                 : reinterpret_cast<int*>(sm + S.off_sd);
-  // after the DP the X buffers hold the traceback scratch
-  int* cuts = reinterpret_cast<int*>(sm + S.off_X);                       // [4 NW][xmax]
-  double* Iw = reinterpret_cast<double*>(sm + S.off_X + S.off_I_rel);     // [xmax+1]
+  // after the DP the traceback scratch (aliased on the X buffers when they
+  // are in shared memory)
+  int* cuts = reinterpret_cast<int*>(sm + S.off_tb);                      // [8 NW or NW][xmax]
+  double* Iw = reinterpret_cast<double*>(sm + S.off_tb + S.off_I_rel);    // [xmax+1]
   const int LS = S.LS;
   const int LX = S.LX;
   const real* Lt;  // L(m) = m ln m, m = 0..n
@@ -521,7 +525,7 @@ k_dp(DPParams P, DPPlan S) {
         // several paths at once, one per group of G lanes, largest l first,
         // G as large as lets every path start in the first round; every path
         // is then re-scored in double.
-        int* lst = reinterpret_cast<int*>(sm + S.off_X + S.off_lst_rel);
+        int* lst = reinterpret_cast<int*>(sm + S.off_tb + S.off_lst_rel);
         if (warp == 0) {
           real cbest = Rget(k, 1);
           int carg = 1;
@@ -739,7 +743,7 @@ typedef void (*dp_kernel_t)(DPParams, DPPlan);
   cudaError_t NAME##_configure(int lev, int smem, int threads, int* blocks_per_sm) {     \
     const dp_kernel_t k = NAME##_pick(lev);                                              \
     const cudaError_t e =                                                                \
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+        allow_dynamic_smem(reinterpret_cast<const void*>(k), smem);     \
     if (e != cudaSuccess) return e;                                                      \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem); \
   }                                                                                      \

@@ -390,12 +390,12 @@ cudaError_t dp_mid_configure(bool fp32, int smem, int threads, int* blocks_per_s
   cudaError_t e = cudaSuccess;
   if (fp32) {
     if (set_attr)
-      e = cudaFuncSetAttribute(k_dp_mid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = allow_dynamic_smem(reinterpret_cast<const void*>(k_dp_mid<float>), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_dp_mid<float>, threads, smem);
   }
   if (set_attr)
-    e = cudaFuncSetAttribute(k_dp_mid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = allow_dynamic_smem(reinterpret_cast<const void*>(k_dp_mid<double>), smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_dp_mid<double>, threads, smem);
 }

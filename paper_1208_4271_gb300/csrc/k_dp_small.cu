@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
 template <typename real>
 static cudaError_t small_cfg(int smem, int threads, int* blocks) {
   const cudaError_t e =
-      cudaFuncSetAttribute(k_dp_small<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      allow_dynamic_smem(reinterpret_cast<const void*>(k_dp_small<real>), smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_dp_small<real>, threads, smem);
 }

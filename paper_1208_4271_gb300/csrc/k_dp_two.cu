@@ -175,11 +175,11 @@ __global__ void __launch_bounds__(256, 2) k_dp_two(DPParams P, int off_rec, int 
 cudaError_t dp_two_configure(bool fp32, int smem, int threads, int* blocks_per_sm) {
   cudaError_t e;
   if (fp32) {
-    e = cudaFuncSetAttribute(k_dp_two<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = allow_dynamic_smem(reinterpret_cast<const void*>(k_dp_two<float>), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_dp_two<float>, threads, smem);
   }
-  e = cudaFuncSetAttribute(k_dp_two<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = allow_dynamic_smem(reinterpret_cast<const void*>(k_dp_two<double>), smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_dp_two<double>, threads, smem);
 }

@@ -383,7 +383,7 @@ cudaError_t dp_warp_configure(int lev, int tdw, int smem, int threads, int* bloc
   const dp_warp_kernel_t k = dp_warp_pick(lev, tdw);
   if (!k) return cudaErrorInvalidValue;
   if (set_attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k), smem);
     if (e != cudaSuccess) return e;
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);

@@ -15,9 +15,10 @@ __global__ void k_final(FinalParams F) {
   if (pl >= F.chunk_pairs) return;
   const int n = F.pp.n_used[pl];
   const int B = F.pp.B[pl];
+  const int64_t pi = pair_index(F.pp, F.pair0 + pl);  // the pair's index in the batch
   gmine_pair_score sc;
   sc.mic = sc.mas = sc.mev = sc.mcn = 0.0;
-  sc.m_offset = (F.pair0 + pl) * F.m_stride;
+  sc.m_offset = pi * F.m_stride;
   sc.n_used = n < 0 ? 0 : n;
   sc.B = B < 0 ? 0 : B;
   sc.m_cells = 0;
@@ -30,12 +31,12 @@ __global__ void k_final(FinalParams F) {
   const int flags = F.pp.flags[pl];
   if ((flags & (1 << GMINE_E_ARG)) || n < 4 || B < 4) {
     sc.status = (flags & (1 << GMINE_E_ARG)) ? GMINE_E_ARG : GMINE_E_TOO_FEW;
-    if (lane == 0) F.scores[F.pair0 + pl] = sc;
+    if (lane == 0) F.scores[pi] = sc;
     return;
   }
   const double* M0 = F.Mo + (pl * 2 + 0) * F.cells_max;
   const double* M1 = F.Mo + (pl * 2 + 1) * F.cells_max;
-  double* Mout = F.M ? F.M + (F.pair0 + pl) * F.m_stride : nullptr;
+  double* Mout = F.M ? F.M + pi * F.m_stride : nullptr;
   int cells = 0;
   for (int y = 2; y <= B / 2; ++y) cells += B / y - 1;
 
@@ -92,7 +93,7 @@ __global__ void k_final(FinalParams F) {
   sc.mcn_xy = mcn_xy;
   sc.m_cells = cells;
   sc.status = (flags & (1 << GMINE_E_CONSTANT)) ? GMINE_E_CONSTANT : GMINE_OK;
-  if (lane == 0) F.scores[F.pair0 + pl] = sc;
+  if (lane == 0) F.scores[pi] = sc;
 }
 
 // Exports for the single-step entry points.

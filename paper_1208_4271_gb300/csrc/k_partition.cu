@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
 cudaError_t partition_configure(bool global, bool wide, int smem, int threads, int* blocks_per_sm) {
   auto k = wide ? k_partition_t<true, uint32_t>
                 : (global ? k_partition_t<true, uint16_t> : k_partition_t<false, uint16_t>);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }

@@ -8,14 +8,17 @@
 
 namespace gm {
 
-__global__ void k_tables(int n, double* L64, float* L32, double* lnt, int B, double c,
+__global__ void k_tables(int nL, double* L64, float* L32, double* lnt, int B, int n, double c,
                          int64_t* rec_off);
+__global__ void k_pair_count(const double* vars, int64_t p, int64_t n, const int32_t* pairs,
+                             int64_t n_pairs, const uint8_t* aidx, const int32_t* Btab,
+                             int64_t btab_stride, int32_t* count);
 __global__ void k_nonfinite(const double* vars, int64_t p, int n, int32_t* nf);
 __global__ void k_pair_prep(const int32_t* pairs, int64_t pair0, int64_t chunk,
                             int64_t p, int n, const int32_t* nf,
                             const int32_t* Btab, PairPrep pp);
 cudaError_t rank_launch(int grid, int threads, int smem, cudaStream_t st, const double* vars,
-                        int64_t p, int n, const int32_t* nf, const int32_t* pairs, int64_t pair0,
+                        int64_t n_row, int n, const int32_t* nf, const int32_t* pairs, int64_t pair0,
                         PairPrep pp, const int32_t* Btab, int64_t slot_base, int64_t nslots,
                         RankData rk, unsigned char* gscr, int64_t gscr_per_cta);
 __global__ void k_equi(int64_t slot_base, int64_t nslots, int64_t p,
@@ -77,5 +80,11 @@ cudaError_t pearson_launch(int grid, cudaStream_t st, const double* d_vars, int6
 
 // Records a CUDA error for gmine_strerror (host code outside gmine_api.cu).
 void note_cuda_error(cudaError_t e);
+
+// Lets `func` launch with `smem` bytes of dynamic shared memory on the
+// current device.  The attribute only ever grows (a high-water mark per
+// kernel and device, under a lock): a call planning a smaller launch never
+// lowers the limit another host thread's planned launch relies on.
+cudaError_t allow_dynamic_smem(const void* func, int smem);
 
 }  // namespace gm

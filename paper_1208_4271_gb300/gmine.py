@@ -76,6 +76,11 @@ def lib():
                                                _i32, _vp, _i64, _vp, _vp, _vp]
         L.gmine_compute_batch_static.argtypes = [_vp, _i64, _i64, _vp, _i64, ctypes.POINTER(Param),
                                                  _i32, _vp, _vp, _vp]
+        L.gmine_plan_uneven.argtypes = [_i64, _i64, _i64, _vp, _i32, ctypes.c_double, _i32,
+                                        ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+        L.gmine_compute_batch_uneven.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp,
+                                                 ctypes.c_double, _i32, _vp, _i64, _vp, _vp,
+                                                 ctypes.POINTER(Trace), _vp]
         L.gmine_rank.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp]
         L.gmine_equipartition.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64, _vp]
         L.gmine_score_pair_host.argtypes = [_vp, _vp, _i64, ctypes.POINTER(Param), _i32, _vp, _vp]
@@ -234,6 +239,66 @@ def compute_batch(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, want_M=
                                           workspace.nbytes, _dptr(scores), _dptr(M),
                                           ctypes.byref(trace), _stream_ptr(stream))
     _check(rc, "gmine_compute_batch")
+    return scores[:n_pairs], M
+
+
+def alpha_table(alphas):
+    """Per-pair alpha values -> (distinct values as a float64 array, uint8
+    index of each pair into it)."""
+    a = np.asarray(alphas, dtype=np.float64).reshape(-1)
+    vals, idx = np.unique(a, return_inverse=True)
+    return np.ascontiguousarray(vals), idx.astype(np.uint8)
+
+
+def plan_uneven(p, n, n_pairs, alpha_values, c=15.0, precision=PLAIN_FP64):
+    vals = np.ascontiguousarray(alpha_values, dtype=np.float64).reshape(-1)
+    cells = _i64(0)
+    ws = _i64(0)
+    _check(lib().gmine_plan_uneven(int(p), int(n), int(n_pairs), vals.ctypes.data_as(_vp), len(vals),
+                                   float(c), int(precision), ctypes.byref(cells), ctypes.byref(ws)),
+           "gmine_plan_uneven")
+    return int(cells.value), int(ws.value)
+
+
+class UnevenWorkspace:
+    """A device workspace for gmine_compute_batch_uneven."""
+
+    def __init__(self, p, n, n_pairs, alpha_values, c=15.0, precision=PLAIN_FP64, device="cuda"):
+        import torch
+        self.cells, self.nbytes = plan_uneven(p, n, n_pairs, alpha_values, c, precision)
+        self.buf = torch.empty(max(self.nbytes, 1), dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+
+def compute_batch_uneven(vars_, pairs, alphas, c=15.0, precision=PLAIN_FP64, want_M=True,
+                         workspace=None, measure=None, stream=None):
+    """Pairs of uneven size, each with its own alpha (gmine_compute_batch_uneven).
+    vars_: CUDA float64 [p, n] (NaN-padded); pairs: CUDA int32 [n_pairs, 2];
+    alphas: one alpha per pair (host sequence).  Returns (scores, M)."""
+    import torch
+    assert vars_.is_cuda and vars_.dtype == torch.float64 and vars_.is_contiguous()
+    assert pairs.is_cuda and pairs.dtype == torch.int32 and pairs.is_contiguous()
+    p, n = vars_.shape
+    n_pairs = pairs.shape[0]
+    vals, idx = alpha_table(alphas)
+    assert idx.size == n_pairs
+    if workspace is None:
+        workspace = UnevenWorkspace(p, n, n_pairs, vals, c, precision, device=vars_.device)
+    aidx = torch.from_numpy(idx).to(vars_.device)
+    scores = torch.empty((max(n_pairs, 1), SCORE_DTYPE.itemsize), dtype=torch.uint8, device=vars_.device)
+    M = None
+    if want_M:
+        M = torch.zeros(max(n_pairs * workspace.cells, 1), dtype=torch.float64, device=vars_.device)
+    rc = lib().gmine_compute_batch_uneven(_dptr(vars_), p, n, _dptr(pairs), n_pairs,
+                                          vals.ctypes.data_as(_vp), len(vals), _dptr(aidx), float(c),
+                                          int(precision), workspace.ptr, workspace.nbytes,
+                                          _dptr(scores), _dptr(M),
+                                          ctypes.byref(measure.trace) if measure is not None else None,
+                                          _stream_ptr(stream))
+    _check(rc, "gmine_compute_batch_uneven")
     return scores[:n_pairs], M
 
 

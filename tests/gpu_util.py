@@ -125,4 +125,21 @@ def compare_pairs(V, P, run, alpha, c, tol, idx=None, ref=None, check_M=True):
         assert errs["mcn"] <= max(tol, 1e-9) or tol > 1e-9
     if tol <= 1e-9:
         assert np.array_equal(s["mcn_xy"][ok], ref["info"][ok, 2]), "mcn_xy"
+    elif check_M and "M" in ref:
+        # the float path's MCN (log2 of the smallest xy whose cell equals its
+        # MIC exactly) is a step function of near-equal scores; what it must
+        # give is a grid whose exact score is within the contract of the
+        # exact MIC: some cell with that xy has oracle M >= MIC - 2 tol
+        worst = 0.0
+        for j, i in enumerate(idx):
+            if ref["status"][j] != gmine.OK:
+                continue
+            B = int(ref["info"][j, 1])
+            cells = oracle.cell_layout(B)
+            Mref = ref["M"][ref["M_offsets"][j]:ref["M_offsets"][j] + len(cells)]
+            xy = int(s["mcn_xy"][j])
+            best = max(m for (cx, cy), m in zip(cells, Mref) if cx * cy == xy)
+            worst = max(worst, float(ref["stats"][j, 0] - best))
+        errs["mcn_cell_gap"] = worst
+        assert worst <= 2 * tol, ("mcn cell", worst)
     return errs

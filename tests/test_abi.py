@@ -81,3 +81,42 @@ def test_pearson_batch_argument_checks(lib):
     assert lib.gmine_pearson_batch(dummy, -1, 10, dummy, 1, None, dummy, None, None) == gmine.E_ARG
     # nothing to do is success without touching a device
     assert lib.gmine_pearson_batch(None, 0, 0, None, 0, None, None, None, None) == gmine.OK
+
+
+def test_uneven_batch_argument_checks(lib):
+    vp = ctypes.c_void_p
+    dummy = vp(16)  # never dereferenced: every call below fails its checks first
+    cells, ws = ctypes.c_int64(0), ctypes.c_int64(0)
+    good = np.array([0.6, 0.75])
+    bad = np.array([0.6, 1.5])
+    many = np.linspace(0.3, 0.9, 9)
+    plan = lib.gmine_plan_uneven
+    assert plan(2, 100, 1, bad.ctypes.data_as(vp), 2, 15.0, 0, ctypes.byref(cells), ctypes.byref(ws)) == gmine.E_PARAM
+    assert plan(2, 100, 1, good.ctypes.data_as(vp), 2, -1.0, 0, ctypes.byref(cells), ctypes.byref(ws)) == gmine.E_PARAM
+    assert plan(2, 100, 1, many.ctypes.data_as(vp), 9, 15.0, 0, ctypes.byref(cells), ctypes.byref(ws)) == gmine.E_LIMIT
+    assert plan(2, 100, 1, None, 1, 15.0, 0, ctypes.byref(cells), ctypes.byref(ws)) == gmine.E_ARG
+    assert plan(2, 100, 1, good.ctypes.data_as(vp), 0, 15.0, 0, ctypes.byref(cells), ctypes.byref(ws)) == gmine.E_ARG
+    run = lib.gmine_compute_batch_uneven
+    # NULL inputs, a missing alpha index array with several alphas, per-task trace arrays
+    assert run(None, 2, 10, dummy, 1, good.ctypes.data_as(vp), 2, dummy, 15.0, 0, dummy, 1 << 20,
+               dummy, None, None, None) == gmine.E_ARG
+    assert run(dummy, 2, 10, dummy, 1, good.ctypes.data_as(vp), 2, None, 15.0, 0, dummy, 1 << 20,
+               dummy, None, None, None) == gmine.E_ARG
+    tr = gmine.Trace(dummy, None, None, None, 0, 0, None, None, 0, 0, None, None, None, None)
+    assert run(dummy, 2, 10, dummy, 1, good.ctypes.data_as(vp), 2, dummy, 15.0, 0, dummy, 1 << 20,
+               dummy, None, ctypes.byref(tr), None) == gmine.E_ARG
+
+
+def test_oracle_per_pair_alpha_batch_equals_single():
+    rng = np.random.default_rng(4)
+    V = rng.normal(size=(8, 150))
+    V[3, ::5] = np.nan
+    P = np.array([[0, 1], [2, 3], [4, 5], [6, 7]], dtype=np.int32)
+    alphas = np.array([0.55, 0.6, 0.75, 0.6])
+    out = oracle.score_batch(V, P, alphas, 15.0, nthreads=2, want_M=True)
+    for i, (a, b) in enumerate(P):
+        r = oracle.score_pair(V[a], V[b], alphas[i], 15.0)
+        assert out["stats"][i].tolist() == [r["mic"], r["mas"], r["mev"], r["mcn"]]
+        assert out["info"][i, 1] == oracle.B_of(r["n_used"], alphas[i])
+        off = out["M_offsets"][i]
+        assert np.array_equal(out["M"][off:off + r["m_cells"]], r["M"])
