@@ -54,6 +54,11 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven batch (20,000 pairs, n in [50, 20000], per-pair alpha)")
+    ap.add_argument("--no-ties", action="store_true",
+                    help="skip the heavy-tie batch (124,750 pairs at n=1340, 200 pairs at n=100000)")
+    ap.add_argument("--uneven-pairs", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -194,6 +199,113 @@ def partition_flips(Vd, dev, nv):
     return {"tasks": int(live.sum()), "differing": int(differ.sum()),
             "fraction": float(differ.mean()) if live.any() else 0.0,
             "sample": "all %d pairs of the first %d variables" % (Ps.shape[0], nv)}
+
+
+def oracle_errors(V, P, alphas, got, idx, threads):
+    """Oracle statistics of the pairs idx and the largest absolute errors of
+    the GPU's MIC, MAS, MEV (and MCN) on them."""
+    import oracle
+    ref = oracle.score_batch(V, P[idx], alphas if np.ndim(alphas) == 0 else alphas[idx], C,
+                             nthreads=threads)
+    ok = ref["status"] == 0
+    out = {}
+    for j, name in enumerate(("mic", "mas", "mev", "mcn")):
+        e = np.abs(np.asarray(got[name][idx], dtype=np.float64) - ref["stats"][:, j])[ok]
+        out[name] = float(e.max()) if e.size else None
+    out["status_equal"] = bool(np.array_equal(np.asarray(got["status"][idx]), ref["status"]))
+    return out
+
+
+def bench_uneven(dev, args, threads, do_parity):
+    """The uneven batch: 20,000 pairs with n log-uniform in [50, 20000], 0-20 %
+    missing samples, alpha per pair in {0.55, 0.6, 0.75}, in one
+    gmine_compute_batch_uneven call (FP32 DP, FP64 re-score), timed with CUDA
+    events around the call (its planning read-back included).  Parity: the
+    oracle on a random sample of the pairs whose DP work stays below a bound
+    (the heaviest pairs take the oracle minutes each)."""
+    import torch
+    from paper_1208_4271_gb300 import gmine, workloads
+    V, P, alphas, ns = workloads.config4(n_pairs=args.uneven_pairs)
+    Vd = torch.from_numpy(V).to(dev)
+    Pd = torch.from_numpy(P).to(dev)
+    prec = gmine.FP32_DP_FP64_RESCORE
+    vals, _ = gmine.alpha_table(alphas)
+    ws = gmine.UnevenWorkspace(V.shape[0], V.shape[1], P.shape[0], vals, C, prec, device=dev)
+    meas = gmine.Measure(device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    scores, _ = gmine.compute_batch_uneven(Vd, Pd, alphas, C, prec, want_M=False, workspace=ws,
+                                           measure=meas)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    s = gmine.scores_to_numpy(scores)
+    out = {"value": P.shape[0] / (ms / 1e3), "unit": "pairs/s", "ms": ms,
+           "workload": "%d pairs, n log-uniform in [50, 20000] (max %d), 0-20%% missing, "
+                       "alpha per pair in {0.55, 0.6, 0.75}, c=15, one call" % (P.shape[0], int(ns.max())),
+           "dp_candidates": int(meas.counters[0].item()), "dp_ms": meas.dp_ms,
+           "dp_launches": meas.dp_launches, "gpu_launches": meas.kernel_launches}
+    if meas.dp_ms > 0:
+        out["dp_tcand_per_s"] = out["dp_candidates"] / (meas.dp_ms / 1e3) / 1e12
+    del ws, Vd
+    torch.cuda.empty_cache()
+    if do_parity:
+        rng = np.random.default_rng(44)
+        light = np.flatnonzero(ns * np.where(alphas > 0.7, 4.0, 1.0) <= 3000)
+        idx = np.sort(rng.choice(light, min(200, light.size), replace=False))
+        t0 = time.perf_counter()
+        out["fp32_vs_oracle"] = oracle_errors(V, P, alphas, s, idx, threads)
+        out["fp32_vs_oracle"]["sample"] = ("%d random pairs with n <= 3000 (n <= 750 at alpha 0.75), "
+                                           "oracle %.1f s" % (idx.size, time.perf_counter() - t0))
+    return out
+
+
+def bench_ties(dev, args, threads, do_parity):
+    """Heavy-tie RNA-seq-shaped batches (negative-binomial counts, log2(c+1)):
+    all 124,750 pairs of 500 variables at n=1340, and 200 pairs of 21
+    variables at n=100,000 (B = 999), alpha=0.6, c=15, FP32 DP with FP64
+    re-score, one gmine_compute_batch each, CUDA events around the call."""
+    import torch
+    from paper_1208_4271_gb300 import gmine, workloads
+    out = {}
+    prec = gmine.FP32_DP_FP64_RESCORE
+    stream = torch.cuda.current_stream(dev)
+    for key, (p, n, npairs) in (("ties_1340", (500, 1340, None)), ("ties_100000", (21, 100000, 200))):
+        V, P = workloads.config5(p=p, n=n)
+        if npairs is not None:
+            P = P[:npairs]
+        Vd = torch.from_numpy(V).to(dev)
+        Pd = torch.from_numpy(np.ascontiguousarray(P)).to(dev)
+        ws = gmine.Workspace(p, n, P.shape[0], ALPHA, C, prec, device=dev)
+        meas = gmine.Measure(device=dev)
+        gmine.compute_batch(Vd, Pd[:min(64, P.shape[0])], ALPHA, C, prec, want_M=False, workspace=ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        scores, _ = gmine.compute_batch(Vd, Pd, ALPHA, C, prec, want_M=False, workspace=ws, trace=meas.trace)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        s = gmine.scores_to_numpy(scores)
+        r = {"value": P.shape[0] / (ms / 1e3), "unit": "pairs/s", "ms": ms,
+             "workload": "%d pairs of %d heavy-tie variables, n=%d" % (P.shape[0], p, n),
+             "dp_candidates": int(meas.counters[0].item()), "dp_ms": meas.dp_ms}
+        if meas.dp_ms > 0:
+            r["dp_tcand_per_s"] = r["dp_candidates"] / (meas.dp_ms / 1e3) / 1e12
+        if do_parity and n <= 1340:
+            rng = np.random.default_rng(55)
+            idx = np.sort(rng.choice(P.shape[0], 2000, replace=False))
+            t0 = time.perf_counter()
+            r["fp32_vs_oracle"] = oracle_errors(V, P, ALPHA, s, idx, threads)
+            r["fp32_vs_oracle"]["sample"] = "2000 random pairs, oracle %.1f s" % (time.perf_counter() - t0)
+        out[key] = r
+        del ws, Vd
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -392,6 +504,15 @@ def main():
                "calls": "mean of 2 host-buffer calls after one warm-up call"}
         del wsh
 
+    # the uneven batch and the heavy-tie batches (their own workspaces; the
+    # main workload's are released first)
+    del ws
+    torch.cuda.empty_cache()
+    threads = os.cpu_count() or 1
+    do_par = rank == 0 and world == 1 and not args.no_cpu_baseline
+    uneven = None if args.no_uneven else bench_uneven(dev, args, threads, do_par)
+    ties = None if args.no_ties else bench_ties(dev, args, threads, do_par)
+
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -472,7 +593,9 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "parity": parity}
+            "parity": parity,
+            "uneven": uneven,
+            "ties": ties}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

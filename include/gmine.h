@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define GMINE_ABI_VERSION 1
+#define GMINE_ABI_VERSION 2
 
 /* status codes */
 #define GMINE_OK 0
@@ -128,6 +128,12 @@ typedef struct {
     int32_t *h_dp_launches;  /* host: number of DP kernel launches timed   */
     int32_t *h_kernel_launches;  /* host: if not NULL, every kernel launch of
                                     the call is counted here               */
+    float *h_launch_ms;   /* host: with h_dp_ms, the milliseconds of each DP
+                             launch in launch order (chunks, then launch
+                             groups as gmine_dp_groups lists them), at most
+                             launch_cap of them                            */
+    int32_t launch_cap;
+    int32_t reserved2;
 } gmine_trace;
 
 /* ---- parameters, errors ------------------------------------------------ */
@@ -146,6 +152,44 @@ int gmine_B(int64_t n, double alpha);
 
 /* Number of cells of M for a given B. */
 int64_t gmine_m_cells(int32_t B);
+
+/* ---- kernel choices of the dynamic program (autotuning) ---------------- */
+
+/* Kernel shapes of the OptimizeXAxis launches (Appendix item 10; SOM Alg. 2). */
+#define GMINE_DP_BLOCKED 0  /* CTA per task, t in blocks of 32, levels in registers */
+#define GMINE_DP_WARP 1     /* warp per task, the same blocked recursion (float only) */
+#define GMINE_DP_MID 2      /* CTA per task, level after level, entropy triangle in
+                               shared memory (8-12 levels) */
+#define GMINE_DP_SMALL 3    /* warp per task, level after level (x <= 5) */
+#define GMINE_DP_TWO 4      /* x = 2: two entropy terms per candidate */
+
+/* One launch group of the DP: the tasks with row counts y in [ylo, yhi],
+   its kernel shape and CTA size (threads); smem and lev are outputs of
+   gmine_dp_groups (dynamic shared memory per CTA, levels per pass). */
+typedef struct {
+    int32_t ylo, yhi;
+    int32_t kind;
+    int32_t threads;
+    int32_t smem;
+    int32_t lev;
+} gmine_dp_choice;
+
+/* The launch groups the planner makes on the current device for a batch
+   of n samples with these parameters, with the kernel shape and CTA size
+   each gets (the built-in rules, or a choice set by gmine_set_dp_choices
+   when it is feasible).  Writes min(*count, cap) entries; *count = number
+   of groups.  GMINE_E_ARG / GMINE_E_PARAM / GMINE_E_LIMIT as gmine_plan. */
+int gmine_dp_groups(int64_t n, double alpha, double c, int32_t precision,
+                    gmine_dp_choice *out, int32_t cap, int32_t *count);
+
+/* Tuned choices for batches with these (n, alpha, c, precision): a choice
+   replaces the built-in rule of the launch group with the same [ylo, yhi]
+   whenever its kernel shape applies to the group and its shared-memory plan
+   fits the device (else the rule stays).  count = 0 removes them.  The
+   table is process-wide and read when a call is planned; gmine_dp_groups
+   shows the effect.  GMINE_E_ARG for a bad kind, range or count. */
+int gmine_set_dp_choices(int64_t n, double alpha, double c, int32_t precision,
+                         const gmine_dp_choice *choices, int32_t count);
 
 /* ---- batch over pairs -------------------------------------------------- */
 

@@ -366,6 +366,34 @@ struct DPTiming {
   }
 };
 
+// Tuned DP choices (gmine_set_dp_choices): per batch shape (n, B, c,
+// precision) the kernel shape and CTA size of launch groups, process-wide.
+struct ChoiceSet {
+  int64_t n;
+  int B;
+  double c;
+  bool fp32;
+  std::vector<gmine_dp_choice> choices;
+};
+std::mutex g_choice_mu;
+std::vector<ChoiceSet> g_choice_sets;
+
+std::vector<gmine_dp_choice> dp_choices_for(int64_t n, int B, double c, bool fp32) {
+  std::lock_guard<std::mutex> lock(g_choice_mu);
+  for (const ChoiceSet& cs : g_choice_sets)
+    if (cs.n == n && cs.B == B && cs.c == c && cs.fp32 == fp32) return cs.choices;
+  return {};
+}
+
+int group_kind(const DPGroup& g) {
+  return g.two ? GMINE_DP_TWO : g.warp ? GMINE_DP_WARP : g.mid ? GMINE_DP_MID
+                 : g.small ? GMINE_DP_SMALL : GMINE_DP_BLOCKED;
+}
+
+int group_smem(const DPGroup& g) {
+  return g.two ? g.smem_two : g.warp ? g.WS.total : g.mid ? g.MS.total : g.small ? g.SS.total : g.S.total;
+}
+
 // The kernel plan of a chunk whose pairs have at most n used samples and B
 // at most Bc (tasks y = 2 .. Bc/2), clump factor c.
 int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, ChunkPlan* cp) {
@@ -393,43 +421,54 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
       g.lev = lev;
     }
   }
+  const std::vector<gmine_dp_choice> forced = dp_choices_for(n, B, c, fp32);
   for (int gi = 0; gi < cp->ngroups; ++gi) {
     DPGroup& g = cp->grp[gi];
     const TaskBounds tg = task_bounds((int)n, B, c, g.ylo, g.yhi);
-    if (g.lev == 2) {
+    const gmine_dp_choice* fc = nullptr;
+    for (const gmine_dp_choice& ch : forced)
+      if (ch.ylo == g.ylo && ch.yhi == g.yhi) fc = &ch;
+    // each kernel shape: planned with CTA size `threads` (0: the size the
+    // rules prefer), applied if its shared-memory plan fits; returns
+    // GMINE_OK and sets *ok, or an error
+    auto try_two = [&](int threads, bool* ok) -> int {
+      *ok = false;
+      if (g.lev != 2) return GMINE_OK;
+      // the L table, then one task record per warp
+      const int off = (int)(((n + 1) * (fp32 ? 4 : 8) + 15) & ~int64_t(15));
+      const int recb = (4 * std::max(tg.rec_max, 4) + 15) & ~15;
+      int th = threads > 0 ? threads : 256;
+      if (threads <= 0)
+        while (th > 32 && off + th / 32 * recb + 1024 > dev.smem_optin) th /= 2;
+      const int smem = off + th / 32 * recb;
+      if (smem + 1024 > dev.smem_optin) return GMINE_OK;
       int blocks = 0;
+      cudaError_t e = dp_two_configure(fp32, smem, th, &blocks);
+      if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+      if (blocks < 1) return GMINE_OK;
       g.two = true;
-      // the L table, then one task record per warp (8 warps, fewer if
-      // shared memory is short)
-      g.off_two_rec = (int)(((n + 1) * (fp32 ? 4 : 8) + 15) & ~int64_t(15));
-      g.two_rec_bytes = (4 * std::max(tg.rec_max, 4) + 15) & ~15;
-      g.threads = 256;
-      while (g.threads > 32 && g.off_two_rec + g.threads / 32 * g.two_rec_bytes + 1024 > dev.smem_optin)
-        g.threads /= 2;
-      g.smem_two = g.off_two_rec + g.threads / 32 * g.two_rec_bytes;
-      if (g.smem_two + 1024 <= dev.smem_optin) {
-        cudaError_t e = dp_two_configure(fp32, g.smem_two, g.threads, &blocks);
-        if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
-        if (blocks < 1) return GMINE_E_LIMIT;
-        g.ctas = blocks * dev.sms;
-        g.scratch_per_cta = 0;
-        continue;
-      }
-      // the table does not fit (very large n): the general kernels take it
-      g.two = false;
-      g.lev = dp_level_group(fp32, 1);
-    }
-    if (fp32 && g.yhi <= 15 && dp_warp_supported(g.lev, 16)) {
-      // a moderate number of levels (float path): one warp per task, the
-      // CTA size that keeps the most warps resident
+      g.off_two_rec = off;
+      g.two_rec_bytes = recb;
+      g.threads = th;
+      g.smem_two = smem;
+      g.ctas = blocks * dev.sms;
+      g.scratch_per_cta = 0;
+      *ok = true;
+      return GMINE_OK;
+    };
+    auto try_warp = [&](int threads, bool* ok) -> int {
+      *ok = false;
+      if (!(fp32 && g.yhi <= 15 && dp_warp_supported(g.lev, 16))) return GMINE_OK;
       const int tdw = ((g.yhi + 1 + 3) & ~3) <= 8 ? 8 : 16;
       int best = 0;
       for (int w : {4, 2, 1}) {
+        if (threads > 0 && 32 * w != threads) continue;
         const WarpPlan wp = make_warp_plan((int)n, tg, g.lev, w);
         if (wp.total + 1024 > dev.smem_optin) continue;
         int blocks = 0;
         const cudaError_t e = dp_warp_configure(g.lev, tdw, wp.total, 32 * w, &blocks, true);
         if (e != cudaSuccess) { last_cuda_error() = e; return GMINE_E_CUDA; }
+        // the CTA size that keeps the most warps resident
         if (blocks * w > best) {
           best = blocks * w;
           g.warp = true;
@@ -440,25 +479,30 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
       }
       if (g.warp) {
         g.scratch_per_cta = 0;
-        continue;
+        *ok = true;
       }
-    }
-    if (g.lev >= 8 && g.lev <= 12) {
-      // few levels, entropy triangle small enough for two CTAs per SM:
-      // level-major kernel (no chain along t)
-      const int th = tg.kmax >= 96 ? 256 : 128;
+      return GMINE_OK;
+    };
+    auto try_mid = [&](int threads, bool* ok) -> int {
+      *ok = false;
+      if (!(g.lev >= 8 && g.lev <= 12)) return GMINE_OK;
+      // the entropy triangle small enough for two CTAs per SM
+      const int th = threads > 0 ? threads : (tg.kmax >= 96 ? 256 : 128);
       const MidPlan mp = make_mid_plan((int)n, tg, fp32, th);
-      if (2 * (mp.total + 1024) <= dev.smem_optin + 1024) {
-        g.mid = true;
-        g.threads = th;
-        g.MS = mp;
-        g.scratch_per_cta = 0;
-        continue;
-      }
-    }
-    if (g.lev <= 4 && tg.kmax <= 256 && tg.xmax <= 9) {
-      // few columns: one warp per task, as many warps per CTA as fit
+      if (2 * (mp.total + 1024) > dev.smem_optin + 1024) return GMINE_OK;
+      g.mid = true;
+      g.threads = th;
+      g.MS = mp;
+      g.scratch_per_cta = 0;
+      *ok = true;
+      return GMINE_OK;
+    };
+    auto try_small = [&](int threads, bool* ok) -> int {
+      *ok = false;
+      if (!(g.lev <= 4 && tg.kmax <= 256 && tg.xmax <= 9)) return GMINE_OK;
+      // as many warps per CTA as fit
       for (int w = 4; w >= 1 && !g.small; w >>= 1) {
+        if (threads > 0 && 32 * w != threads) continue;
         const SmallPlan sp = make_small_plan((int)n, tg, fp32, w);
         if (sp.total + 1024 <= dev.smem_optin) {
           g.small = true;
@@ -468,21 +512,24 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
       }
       if (g.small) {
         g.scratch_per_cta = 0;
-        continue;
+        *ok = true;
       }
-    }
-    // CTA size: the one that keeps more warps resident per SM (more CTAs,
-    // i.e. more tasks in flight, on a tie: their sequential parts overlap)
-    {
+      return GMINE_OK;
+    };
+    auto try_blocked = [&](int threads, bool* ok) -> int {
+      *ok = false;
+      // CTA size: the one that keeps more warps resident per SM (more CTAs,
+      // i.e. more tasks in flight, on a tie: their sequential parts overlap)
       int best_warps = -1;
       for (int th : {kDPThreadsSmall, kDPThreadsBig}) {
+        if (threads > 0 && th != threads) continue;
         bool rsm = false;
         const DPPlan S = make_dp_plan((int)n, tg, fp32, th, dev.smem_optin, &rsm);
         if (S.total > dev.smem_optin) continue;
         if (th > dp_max_threads(fp32, rsm, g.lev)) continue;  // the instance's launch bound
         int blocks = 0;
-        rc = dp_occupancy(fp32, rsm, g.lev, std::max(S.total, 1), th, &blocks);
-        if (rc != GMINE_OK) return rc;
+        const int r = dp_occupancy(fp32, rsm, g.lev, std::max(S.total, 1), th, &blocks);
+        if (r != GMINE_OK) return r;
         if (blocks * th / 32 > best_warps) {
           best_warps = blocks * th / 32;
           g.threads = th;
@@ -491,14 +538,48 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
           g.ctas = blocks * dev.sms;
         }
       }
-      if (best_warps <= 0) return GMINE_E_LIMIT;
+      if (best_warps <= 0) return GMINE_OK;
       // the launch attribute must allow the chosen plan (the loop left the
       // last candidate's size in place)
       int blocks = 0;
-      rc = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
+      const int r = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &blocks);
+      if (r != GMINE_OK) return r;
+      g.scratch_per_cta = dp_scratch(g.S, g.rsm);
+      *ok = true;
+      return GMINE_OK;
+    };
+    bool ok = false;
+    if (fc) {
+      // a tuned choice for this group, applied when it is feasible here (a
+      // general kernel for x = 2 takes the smallest level group)
+      const int lev0 = g.lev;
+      if (fc->kind != GMINE_DP_TWO && g.lev == 2) g.lev = dp_level_group(fp32, 1);
+      switch (fc->kind) {
+        case GMINE_DP_TWO: rc = try_two(fc->threads, &ok); break;
+        case GMINE_DP_WARP: rc = try_warp(fc->threads, &ok); break;
+        case GMINE_DP_MID: rc = try_mid(fc->threads, &ok); break;
+        case GMINE_DP_SMALL: rc = try_small(fc->threads, &ok); break;
+        case GMINE_DP_BLOCKED: rc = try_blocked(fc->threads, &ok); break;
+        default: break;
+      }
       if (rc != GMINE_OK) return rc;
+      if (ok) continue;
+      g.lev = lev0;
     }
-    g.scratch_per_cta = dp_scratch(g.S, g.rsm);
+    // the rules: x = 2 has a kernel of its own; a moderate number of levels
+    // on the float path one warp per task; 8-12 levels the level-major
+    // kernel; few columns the warp-per-task level-major kernel; else blocked
+    rc = try_two(0, &ok);
+    if (rc != GMINE_OK) return rc;
+    if (ok) continue;
+    if (g.lev == 2) g.lev = dp_level_group(fp32, 1);  // the table does not fit (very large n)
+    for (auto f : {0, 1, 2, 3}) {
+      rc = f == 0 ? try_warp(0, &ok) : f == 1 ? try_mid(0, &ok) : f == 2 ? try_small(0, &ok)
+                                                                          : try_blocked(0, &ok);
+      if (rc != GMINE_OK) return rc;
+      if (ok) break;
+    }
+    if (!ok) return GMINE_E_LIMIT;
   }
   for (int gi = 0; gi < cp->ngroups; ++gi) {
     // an instance of the blocked kernel can serve several groups (row counts
@@ -995,6 +1076,9 @@ int finish_trace(const BatchCtx& b) {
     GM_CUDA(b.timing->total_ms(&ms));
     *b.trace->h_dp_ms = ms;
     if (b.trace->h_dp_launches) *b.trace->h_dp_launches = b.timing->launches();
+    if (b.trace->h_launch_ms)
+      for (int i = 0; i < b.timing->launches() && i < b.trace->launch_cap; ++i)
+        GM_CUDA(cudaEventElapsedTime(&b.trace->h_launch_ms[i], b.timing->ev[2 * i], b.timing->ev[2 * i + 1]));
   }
   return GMINE_OK;
 }
@@ -1207,6 +1291,51 @@ const char* gmine_strerror(int status) {
 int gmine_B(int64_t n, double alpha) { return n > 0 ? host_B(n, alpha) : 0; }
 
 int64_t gmine_m_cells(int32_t B) { return host_cells(B); }
+
+int gmine_dp_groups(int64_t n, double alpha, double c, int32_t precision, gmine_dp_choice* out,
+                    int32_t cap, int32_t* count) {
+  if (!count || (cap > 0 && !out) || n < 0) return GMINE_E_ARG;
+  const gmine_param prm{alpha, c};
+  if (gmine_check_param(&prm) != GMINE_OK) return GMINE_E_PARAM;
+  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
+  if (n > kMaxN) return GMINE_E_LIMIT;
+  DeviceInfo dev;
+  int rc = device_info(&dev);
+  if (rc != GMINE_OK) return rc;
+  ChunkPlan cp;
+  rc = plan_chunk(n, n > 0 ? host_B(n, alpha) : 0, c, precision == GMINE_FP32_DP_FP64_RESCORE, dev, &cp);
+  if (rc != GMINE_OK) return rc;
+  *count = cp.ngroups;
+  for (int gi = 0; gi < cp.ngroups && gi < cap; ++gi) {
+    const DPGroup& g = cp.grp[gi];
+    out[gi] = gmine_dp_choice{g.ylo, g.yhi, group_kind(g), g.threads, group_smem(g), g.lev};
+  }
+  return GMINE_OK;
+}
+
+int gmine_set_dp_choices(int64_t n, double alpha, double c, int32_t precision,
+                         const gmine_dp_choice* choices, int32_t count) {
+  if (n < 0 || count < 0 || (count > 0 && !choices) || count > kMaxDPGroups) return GMINE_E_ARG;
+  const gmine_param prm{alpha, c};
+  if (gmine_check_param(&prm) != GMINE_OK) return GMINE_E_PARAM;
+  if (precision != GMINE_PLAIN_FP64 && precision != GMINE_FP32_DP_FP64_RESCORE) return GMINE_E_ARG;
+  for (int i = 0; i < count; ++i)
+    if (choices[i].kind < GMINE_DP_BLOCKED || choices[i].kind > GMINE_DP_TWO || choices[i].threads < 0 ||
+        choices[i].ylo < 2 || choices[i].yhi < choices[i].ylo)
+      return GMINE_E_ARG;
+  const int B = n > 0 ? host_B(n, alpha) : 0;
+  const bool fp32 = precision == GMINE_FP32_DP_FP64_RESCORE;
+  std::lock_guard<std::mutex> lock(g_choice_mu);
+  for (size_t i = 0; i < g_choice_sets.size(); ++i)
+    if (g_choice_sets[i].n == n && g_choice_sets[i].B == B && g_choice_sets[i].c == c &&
+        g_choice_sets[i].fp32 == fp32) {
+      g_choice_sets.erase(g_choice_sets.begin() + (long)i);
+      break;
+    }
+  if (count > 0)
+    g_choice_sets.push_back(ChoiceSet{n, B, c, fp32, std::vector<gmine_dp_choice>(choices, choices + count)});
+  return GMINE_OK;
+}
 
 int gmine_plan(int64_t p, int64_t n, int64_t n_pairs, const gmine_param* param, int32_t precision,
                int32_t flags, int64_t* m_cells_per_pair, int64_t* workspace_bytes) {

@@ -102,6 +102,27 @@ __device__ __forceinline__ real entropy_reg(const real* __restrict__ Lt, const i
   return e;
 }
 
+// E(s,t) with row t in registers for a fixed row width SWC (4 or 8): the
+// columns beyond yhat are 0 in both rows, and L(0) = 0, so the extra terms
+// subtract exactly zero; no branch on yhat.
+template <typename real, int SWC>
+__device__ __forceinline__ real entropy_regc(const real* __restrict__ Lt, const int* __restrict__ sd,
+                                             const int (&td)[8], int s) {
+  const int4 a = *reinterpret_cast<const int4*>(sd + s * SWC);
+  real e = Lt[td[0] - a.x];
+  e -= Lt[td[1] - a.y];
+  e -= Lt[td[2] - a.z];
+  e -= Lt[td[3] - a.w];
+  if constexpr (SWC == 8) {
+    const int4 b = *reinterpret_cast<const int4*>(sd + s * SWC + 4);
+    e -= Lt[td[4] - b.x];
+    e -= Lt[td[5] - b.y];
+    e -= Lt[td[6] - b.z];
+    e -= Lt[td[7] - b.w];
+  }
+  return e;
+}
+
 // max(a, b, c) in one instruction (three-operand max.f32 of sm_100 and later)
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
@@ -131,7 +152,9 @@ __device__ __forceinline__ unsigned long long splat_x2(float e) {
 // per iteration: each level takes both candidates in one three-operand max
 // (in float two levels share one packed subtraction), and the E pair of the
 // next iteration is formed meanwhile.
-template <typename real, int LEV, bool REG>
+// REG: 4 or 8 = row t in registers, that many columns; 1 = row t in
+// registers, yhat terms; 0 = both rows from shared memory.
+template <typename real, int LEV, int REG>
 __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
                                            int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
                                            const int* __restrict__ sd, int SW, int yhat,
@@ -139,7 +162,8 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   auto E = [&](int s) -> real {
-    if constexpr (REG) return entropy_reg<real>(Lt, sd, SW, yhat, td, s);
+    if constexpr (REG == 4 || REG == 8) return entropy_regc<real, REG>(Lt, sd, td, s);
+    else if constexpr (REG == 1) return entropy_reg<real>(Lt, sd, SW, yhat, td, s);
     else return entropy_term<real>(Lt, sd, SW, yhat, s, tt);
   };
   int s = s_lo;
@@ -217,7 +241,8 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
                         const int* __restrict__ sd, int SW, int yhat,
                         int tt, bool tv, typename Bits<real>::U* Xrow, int warp, int NW, int lane) {
   using BT = Bits<real>;
-  const int CH = stealing ? 8 : 4;  // s per grab
+  constexpr bool fp32 = sizeof(real) == 4;
+  const int CH = stealing ? 16 : 4;  // s per grab
   const int nlev = lmax - 1;
   const int npass = (nlev + LEV - 1) / LEV;
   const int nsb = (s_end - s_begin + CH - 1) / CH;  // s-chunks per pass
@@ -247,10 +272,16 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
     }
     const int s_lo = s_begin + sb * CH;
     const int s_hi = min(s_end - 1, s_lo + CH - 1);
-    if (reg)
-      accumulate<real, LEV, true>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+    // float: the row width's fixed number of terms, no branch on yhat; double:
+    // only yhat terms (the padding terms would cost FP64 issue slots)
+    if (reg && fp32 && SW == 4)
+      accumulate<real, LEV, 4>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+    else if (reg && fp32)
+      accumulate<real, LEV, 8>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+    else if (reg)
+      accumulate<real, LEV, 1>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
     else
-      accumulate<real, LEV, false>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+      accumulate<real, LEV, 0>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
     if (!stealing) g += NW;
   }
   if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
@@ -331,23 +362,37 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
 #pragma unroll 1
   for (int l = 2; l <= lmax; ++l) {
     real* rb = rbuf + par * 32;
+    // the partial maximum from the earlier blocks does not depend on the
+    // chain: read it before the broadcast
+    const real xl = has_x ? BT::from(xr[l - 1]) : BT::ninf();
     rb[lane] = rcur;
     __syncwarp();
-    real m0 = has_x ? BT::from(xr[l - 1]) : BT::ninf();
-    real m1 = BT::ninf();
+    // four independent running maxima (shorter dependency chains); the
+    // maximum is exact, so their order does not change the result
+    real m0 = xl, m1 = BT::ninf(), m2 = BT::ninf(), m3 = BT::ninf();
 #pragma unroll
     for (int q = 0; q < 32 / VW; ++q) {
       if constexpr (sizeof(real) == 4) {
         const float4 r = reinterpret_cast<const float4*>(rb)[q];
-        m0 = fmax3(m0, r.x - ec[4 * q + 0], r.y - ec[4 * q + 1]);
-        m1 = fmax3(m1, r.z - ec[4 * q + 2], r.w - ec[4 * q + 3]);
+        if (q & 1) {
+          m2 = fmax3(m2, r.x - ec[4 * q + 0], r.y - ec[4 * q + 1]);
+          m3 = fmax3(m3, r.z - ec[4 * q + 2], r.w - ec[4 * q + 3]);
+        } else {
+          m0 = fmax3(m0, r.x - ec[4 * q + 0], r.y - ec[4 * q + 1]);
+          m1 = fmax3(m1, r.z - ec[4 * q + 2], r.w - ec[4 * q + 3]);
+        }
       } else {
         const double2 r = reinterpret_cast<const double2*>(rb)[q];
-        m0 = BT::max(m0, r.x - ec[2 * q + 0]);
-        m1 = BT::max(m1, r.y - ec[2 * q + 1]);
+        if (q & 1) {
+          m2 = BT::max(m2, r.x - ec[2 * q + 0]);
+          m3 = BT::max(m3, r.y - ec[2 * q + 1]);
+        } else {
+          m0 = BT::max(m0, r.x - ec[2 * q + 0]);
+          m1 = BT::max(m1, r.y - ec[2 * q + 1]);
+        }
       }
     }
-    const real v = BT::max(m0, m1);
+    const real v = BT::max(fmax3(m0, m1, m2), m3);
     if (tv) {
       if (l != lmax) Rt[t * LS + (l - 1)] = v;
       else if (t == k) *Rtop = v;  // the last level is read at t = k only

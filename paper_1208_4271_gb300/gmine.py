@@ -42,7 +42,18 @@ class Trace(ctypes.Structure):
                 ("d_cuts", ctypes.c_void_p), ("d_I", ctypes.c_void_p),
                 ("I_stride", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("d_counters", ctypes.c_void_p), ("h_dp_ms", ctypes.c_void_p),
-                ("h_dp_launches", ctypes.c_void_p), ("h_kernel_launches", ctypes.c_void_p)]
+                ("h_dp_launches", ctypes.c_void_p), ("h_kernel_launches", ctypes.c_void_p),
+                ("h_launch_ms", ctypes.c_void_p), ("launch_cap", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
+
+
+DP_BLOCKED, DP_WARP, DP_MID, DP_SMALL, DP_TWO = range(5)
+DP_KIND_NAMES = {DP_BLOCKED: "blocked", DP_WARP: "warp", DP_MID: "mid", DP_SMALL: "small", DP_TWO: "two"}
+
+
+class DPChoice(ctypes.Structure):
+    _fields_ = [("ylo", ctypes.c_int32), ("yhi", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("smem", ctypes.c_int32), ("lev", ctypes.c_int32)]
 
 
 _lib = None
@@ -81,6 +92,10 @@ def lib():
         L.gmine_compute_batch_uneven.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp,
                                                  ctypes.c_double, _i32, _vp, _i64, _vp, _vp,
                                                  ctypes.POINTER(Trace), _vp]
+        L.gmine_dp_groups.argtypes = [_i64, ctypes.c_double, ctypes.c_double, _i32,
+                                      ctypes.POINTER(DPChoice), _i32, ctypes.POINTER(_i32)]
+        L.gmine_set_dp_choices.argtypes = [_i64, ctypes.c_double, ctypes.c_double, _i32,
+                                           ctypes.POINTER(DPChoice), _i32]
         L.gmine_rank.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp]
         L.gmine_equipartition.argtypes = [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64, _vp]
         L.gmine_score_pair_host.argtypes = [_vp, _vp, _i64, ctypes.POINTER(Param), _i32, _vp, _vp]
@@ -177,7 +192,7 @@ def alloc_trace(n_pairs, n, alpha, c, device="cuda"):
     t["counters"] = torch.zeros(2, dtype=torch.int64, device=device)
     tr = Trace(_dptr(t["k"]), _dptr(t["yhat"]), _dptr(t["clumps"]), _dptr(t["sc_ends"]),
                st["sc_stride"], st["cut_stride"], _dptr(t["cuts"]), _dptr(t["I"]),
-               st["I_stride"], 0, _dptr(t["counters"]), None, None, None)
+               st["I_stride"], 0, _dptr(t["counters"]), None, None, None, None, 0, 0)
     t.update(st)
     return tr, t
 
@@ -185,18 +200,25 @@ def alloc_trace(n_pairs, n, alpha, c, device="cuda"):
 class Measure:
     """Counters and DP kernel timing of one batch call (gmine_trace without
     the per-task tables): subtract-and-max steps, tasks, summed DP kernel
-    milliseconds measured with CUDA events on the call's stream."""
+    milliseconds measured with CUDA events on the call's stream, and the
+    milliseconds of each DP launch (up to launch_cap)."""
 
-    def __init__(self, device="cuda"):
+    def __init__(self, device="cuda", launch_cap=4096):
         import torch
         self.counters = torch.zeros(2, dtype=torch.int64, device=device)
         self._ms = ctypes.c_double(0.0)
         self._launches = ctypes.c_int32(0)
         self._kernels = ctypes.c_int32(0)
+        self._launch_ms = np.zeros(launch_cap, dtype=np.float32)
         self.trace = Trace(None, None, None, None, 0, 0, None, None, 0, 0,
                            _dptr(self.counters), ctypes.cast(ctypes.byref(self._ms), ctypes.c_void_p),
                            ctypes.cast(ctypes.byref(self._launches), ctypes.c_void_p),
-                           ctypes.cast(ctypes.byref(self._kernels), ctypes.c_void_p))
+                           ctypes.cast(ctypes.byref(self._kernels), ctypes.c_void_p),
+                           self._launch_ms.ctypes.data_as(ctypes.c_void_p), launch_cap, 0)
+
+    @property
+    def launch_ms(self):
+        return self._launch_ms[:min(self._launches.value, self._launch_ms.size)].copy()
 
     @property
     def dp_ms(self):
@@ -209,6 +231,27 @@ class Measure:
     @property
     def kernel_launches(self):
         return self._kernels.value
+
+
+def dp_groups(n, alpha=0.6, c=15.0, precision=PLAIN_FP64):
+    """The DP launch groups planned on the current device: a list of dicts
+    (ylo, yhi, kind, threads, smem, lev)."""
+    cap = 64
+    arr = (DPChoice * cap)()
+    cnt = _i32(0)
+    _check(lib().gmine_dp_groups(int(n), float(alpha), float(c), int(precision), arr, cap,
+                                 ctypes.byref(cnt)), "gmine_dp_groups")
+    return [{f: int(getattr(arr[i], f)) for f, _ in DPChoice._fields_} for i in range(min(cnt.value, cap))]
+
+
+def set_dp_choices(n, alpha, c, precision, choices):
+    """Tuned (ylo, yhi, kind, threads) choices for batches of this shape
+    (an empty list removes them)."""
+    arr = (DPChoice * max(len(choices), 1))()
+    for i, ch in enumerate(choices):
+        arr[i] = DPChoice(int(ch["ylo"]), int(ch["yhi"]), int(ch["kind"]), int(ch["threads"]), 0, 0)
+    _check(lib().gmine_set_dp_choices(int(n), float(alpha), float(c), int(precision), arr, len(choices)),
+           "gmine_set_dp_choices")
 
 
 def compute_batch(vars_, pairs, alpha=0.6, c=15.0, precision=PLAIN_FP64, want_M=True,

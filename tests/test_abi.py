@@ -35,9 +35,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_struct_sizes(lib):
-    assert lib.gmine_abi_version() == 1
+    assert lib.gmine_abi_version() == 2
     assert gmine.SCORE_DTYPE.itemsize == 72
-    assert ctypes.sizeof(gmine.Trace) == 96
+    assert ctypes.sizeof(gmine.Trace) == 112
+    assert ctypes.sizeof(gmine.DPChoice) == 24
 
 
 def test_check_param_matches_documented_ranges(lib):
@@ -102,7 +103,7 @@ def test_uneven_batch_argument_checks(lib):
                dummy, None, None, None) == gmine.E_ARG
     assert run(dummy, 2, 10, dummy, 1, good.ctypes.data_as(vp), 2, None, 15.0, 0, dummy, 1 << 20,
                dummy, None, None, None) == gmine.E_ARG
-    tr = gmine.Trace(dummy, None, None, None, 0, 0, None, None, 0, 0, None, None, None, None)
+    tr = gmine.Trace(dummy, None, None, None, 0, 0, None, None, 0, 0, None, None, None, None, None, 0, 0)
     assert run(dummy, 2, 10, dummy, 1, good.ctypes.data_as(vp), 2, dummy, 15.0, 0, dummy, 1 << 20,
                dummy, None, ctypes.byref(tr), None) == gmine.E_ARG
 
