@@ -34,8 +34,10 @@ C = 15.0
 N_SAMPLES = 1340
 N_VARS = 2000
 L2_FLUSH_BYTES = 256 << 20
-# FP64 instructions an SM issues per clock on GB300 (its nominal 1.25 TFLOP/s
-# of FP64 FMA at about 2.07 GHz over 152 SMs: 1.25e12 / 2 / 152 / 2.07e9 = 2)
+# FP64 operations (thread instructions) an SM executes per clock on GB300:
+# ncu reports sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained =
+# 2 per SM and cycle (152 SMs x 2 x 2.07 GHz x 2 flops = the nominal 1.25
+# TFLOP/s of FP64 FMA)
 FP64_PER_SM_CLK = 2
 
 
@@ -356,7 +358,10 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1208_4271_gb300 import gmine
+    from paper_1208_4271_gb300 import gmine, tune
+    # the DP launch choices the autotuner measured on this device, if any
+    # (paper_1208_4271_gb300/tuned_dp.json; the planner's rules otherwise)
+    tuned_shapes = tune.apply()
 
     V, P = workload(rank, args.vars)
     p, n = V.shape
@@ -560,15 +565,16 @@ def main():
     dp_launch_ms = dp_ms / max(dp_launches, 1)
     achieved = (cand / max(dp_launches, 1)) / (dp_launch_ms / 1e3) / 1e12 if dp_ms > 0 else 0.0
     if fp64 is not None:
-        # ALU ceiling of the double DP: one DADD and one DMNMX per candidate
-        # on the FP64 pipe, FP64_PER_SM_CLK of them per SM and clock
-        peak64 = sms * FP64_PER_SM_CLK * fmax * 1e6 / 2.0 / 1e12
+        # ceiling of the double DP: one DADD per candidate on the FP64 pipe
+        # (the maxima run on the integer pipe as minima of the bit patterns),
+        # FP64_PER_SM_CLK of them per SM and clock
+        peak64 = sms * FP64_PER_SM_CLK * fmax * 1e6 / 1.0 / 1e12
         ach64 = (fp64["dp_candidates_per_step"] / (fp64["dp_kernel_ms_per_step"] / 1e3) / 1e12
                  if fp64["dp_kernel_ms_per_step"] > 0 else 0.0)
         fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "Tcand/s",
                             "frac": ach64 / peak64,
-                            "peak_basis": "%d SMs x %d FP64 instr/clk x %.0f MHz / 2 instr per DP step "
-                                          "(DADD + DMNMX)" % (sms, FP64_PER_SM_CLK, fmax)}
+                            "peak_basis": "%d SMs x %d FP64 ops/clk x %.0f MHz / 1 FP64 op per DP step "
+                                          "(DADD; the max on the integer pipe)" % (sms, FP64_PER_SM_CLK, fmax)}
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -577,6 +583,8 @@ def main():
                                    "expression, 40 co-regulated modules), alpha=%g, c=%g"
                                    % (p, n, ALPHA, C),
                        "pairs_per_gpu": npairs, "dp": "fp32 with int32 counts, fp64 re-score",
+                       "dp_plan": ("autotuned (%d cached shapes of this device applied)" % tuned_shapes
+                                   if tuned_shapes else "planner rules"),
                        "l2": "256 MiB buffer written between timed steps"},
             "plain_fp64": fp64,
             "linear": linear,

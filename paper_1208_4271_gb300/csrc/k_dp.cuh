@@ -43,13 +43,22 @@ struct Bits<float> {
   __device__ static float ninf() { return __int_as_float(0xff800000); }
   __device__ static float max(float a, float b) { return fmaxf(a, b); }
 };
+// Every value the DP compares -- R, W, their candidates R - E (E >= +0) and
+// the -inf of unused levels -- lies in [-inf, -0.0]: a sum of negated
+// entropy terms.  On that range the order of the values is the reverse of
+// the order of their bit patterns, so the maximum of doubles is the minimum
+// of their 64-bit patterns.  That runs on the integer pipe; GB300's FP64 pipe
+// executes two operations per clock and SM, and is left the subtractions.
 template <>
 struct Bits<double> {
   using U = unsigned long long;
   __device__ static U of(double v) { return (U)__double_as_longlong(v); }
   __device__ static double from(U b) { return __longlong_as_double((long long)b); }
   __device__ static double ninf() { return __longlong_as_double((long long)0xfff0000000000000ull); }
-  __device__ static double max(double a, double b) { return fmax(a, b); }
+  __device__ static double max(double a, double b) {
+    const U x = of(a), y = of(b);
+    return from(y < x ? y : x);
+  }
 };
 
 // The superclump data of a task in shared memory, s-major: row s holds
@@ -129,7 +138,9 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
   return d;
 }
-__device__ __forceinline__ double fmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double fmax3(double a, double b, double c) {
+  return Bits<double>::max(Bits<double>::max(a, b), c);  // values in [-inf, -0.0]
+}
 
 // (r0 - e, r1 - e) for two floats packed in 64 bits (r0 in the low half)
 // in one instruction (sub.f32x2 of sm_100 and later); each element rounds
