@@ -39,6 +39,11 @@ L2_FLUSH_BYTES = 256 << 20
 # 2 per SM and cycle (152 SMs x 2 x 2.07 GHz x 2 flops = the nominal 1.25
 # TFLOP/s of FP64 FMA)
 FP64_PER_SM_CLK = 2
+# DRAM bytes (read + write) per DP task of the float DP launches, from the
+# ncu launch list of the 60-variable case (profiles/launches_config3_60vars.md:
+# 1,200 MB for 254,880 tasks); the launches read their task records and
+# little else, so the traffic scales with the tasks
+DP_DRAM_BYTES_PER_TASK = 4.7e3
 
 
 def parse():
@@ -589,7 +594,12 @@ def main():
             "plain_fp64": fp64,
             "linear": linear,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcand/s",
-                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "frac": achieved / peak if peak else None,
+                         "traffic": DP_DRAM_BYTES_PER_TASK * (tasks / max(args.steps, 1))
+                                    / max(dp_launches // max(args.steps, 1), 1),
+                         "traffic_basis": "bytes per average DP launch: %.1f KB per task (ncu, 60-variable "
+                                          "launch list) x tasks per step / DP launches per step"
+                                          % (DP_DRAM_BYTES_PER_TASK / 1e3),
                          "kernel": "OptimizeXAxis DP launches (k_dp, k_dp_warp, k_dp_mid, k_dp_small, k_dp_two)",
                          "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 1 instr per DP step "
                                        "(half a packed sub.f32x2 + half a 3-operand max)" % (sms, fmax),

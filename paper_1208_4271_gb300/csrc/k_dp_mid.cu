@@ -30,13 +30,20 @@ struct MBits<float> {
   __device__ static float ninf() { return __int_as_float(0xff800000); }
   __device__ static float max(float a, float b) { return fmaxf(a, b); }
 };
+// The values compared here (R, its candidates R - E with E >= +0, -inf)
+// lie in [-inf, -0.0], where the order of doubles is the reverse of the
+// order of their bit patterns: the maximum is an integer minimum, on the
+// integer pipe instead of GB300's two FP64 operations per clock and SM.
 template <>
 struct MBits<double> {
   using U = unsigned long long;
   __device__ static U of(double v) { return (U)__double_as_longlong(v); }
   __device__ static double from(U b) { return __longlong_as_double((long long)b); }
   __device__ static double ninf() { return __longlong_as_double((long long)0xfff0000000000000ull); }
-  __device__ static double max(double a, double b) { return fmax(a, b); }
+  __device__ static double max(double a, double b) {
+    const U x = of(a), y = of(b);
+    return from(y < x ? y : x);
+  }
 };
 
 __device__ __forceinline__ float mid_max3(float a, float b, float c) {
@@ -44,7 +51,9 @@ __device__ __forceinline__ float mid_max3(float a, float b, float c) {
   asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
   return d;
 }
-__device__ __forceinline__ double mid_max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double mid_max3(double a, double b, double c) {
+  return MBits<double>::max(MBits<double>::max(a, b), c);  // values in [-inf, -0.0]
+}
 
 // E(s,t) = L(c_t - c_s) - sum_r L(cum[r][t] - cum[r][s]), increasing r
 template <typename real>

@@ -18,6 +18,19 @@
 
 namespace gm {
 
+// a > b and a == b for the values the W recursion compares (W, W - E with
+// E >= +0, -inf), which lie in [-inf, -0.0]: doubles through their bit
+// patterns on the integer pipe (on that range the order of the patterns is
+// the reverse of the order of the values), floats directly.
+__device__ __forceinline__ bool gt_neg(float a, float b) { return a > b; }
+__device__ __forceinline__ bool gt_neg(double a, double b) {
+  return (unsigned long long)__double_as_longlong(a) < (unsigned long long)__double_as_longlong(b);
+}
+__device__ __forceinline__ bool eq_neg(float a, float b) { return a == b; }
+__device__ __forceinline__ bool eq_neg(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
 namespace {
 
 template <typename real>
@@ -196,14 +209,14 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
           const int s_hi = min(t0 + 31, k);  // the warp's bound: s < the largest t
           for (int s = l - 1; s < s_hi; ++s) {
             const real v = W[s * LW + (l - 1)] - Et[tri_row(s, k) + tt - s - 1];
-            if (s < t && v > best) {
+            if (s < t && gt_neg(v, best)) {
               best = v;
               arg = s;
             }
           }
           if (t <= k) {
             const real wt = W[t * LW + (l - 1)];  // s = t, the empty column
-            if (wt > best) {
+            if (gt_neg(wt, best)) {
               best = wt;
               arg = t;
             }
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
         for (int s = l - 1 + lane; s <= k; s += 32) {
           const real wv = W[s * LW + (l - 1)];
           const real v = s < k ? wv - Et[tri_row(s, k) + k - s - 1] : wv;
-          if (v > best) {
+          if (gt_neg(v, best)) {
             best = v;
             arg = s;
           }
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
         for (int d = 16; d > 0; d >>= 1) {
           const real ob = __shfl_xor_sync(0xffffffffu, best, d);
           const int oa = __shfl_xor_sync(0xffffffffu, arg, d);
-          if (ob > best || (ob == best && oa < arg)) {
+          if (gt_neg(ob, best) || (eq_neg(ob, best) && oa < arg)) {
             best = ob;
             arg = oa;
           }
