@@ -111,19 +111,21 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   const int64_t I_b = (8LL * (S.xmax + 1) + 15) & ~int64_t(15);
   const int64_t lst_b = 4LL * (S.xmax + 1);
   const int64_t tb_bytes = cuts_b + I_b + lst_b;
-  S.off_I_rel = (int)cuts_b;
-  S.off_lst_rel = (int)(cuts_b + I_b);
   const int64_t xrows = (int64_t)2 * 32 * S.LX * rs;
   const int64_t sdbytes = 4LL * std::max(tb.sd_max, 4);
   const int reserve = 1024;
   // Shared memory: the X rows (or the traceback scratch aliased on them),
   // the in-block triangle, two R buffers of 32, R(k, lmax), the superclump
   // rows; with room for it, also the L table and the R table.
+  // (with the X rows in global memory, the traceback's path buffers go
+  // there too: hundreds of levels make them as large as the X rows)
   auto place = [&](bool x_smem, bool sd_smem) -> int64_t {
     int64_t fixed = 0;
     auto add = [&](int64_t b) { const int64_t at = fixed; fixed = (fixed + b + 15) & ~int64_t(15); return (int)at; };
     S.off_X = x_smem ? add(std::max<int64_t>(xrows, tb_bytes)) : -1;
-    S.off_tb = x_smem ? S.off_X : add(tb_bytes);
+    S.off_I_rel = x_smem ? (int)cuts_b : 0;
+    S.off_lst_rel = x_smem ? (int)(cuts_b + I_b) : (int)I_b;
+    S.off_tb = x_smem ? S.off_X : add(I_b + lst_b);
     S.off_Eb = add((int64_t)(32 * 31 / 2) * rs);  // the in-block triangle
     S.off_rbuf = add((int64_t)2 * 32 * rs);
     S.off_Rtop = add((int64_t)rs);  // R(k, lmax)
@@ -140,11 +142,24 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   int64_t scr = align256((int64_t)(tb.kmax + 2) * S.LS * rs);
   S.x_scr_off = -1;
   S.sd_scr_off = -1;
+  S.cuts_scr_off = -1;
   if (!in_smem && fixed + reserve > smem_optin) {
     fixed = place(false, true);
     S.x_scr_off = scr;
     scr = align256(scr + xrows);
-    if (fixed + reserve > smem_optin) {
+    S.cuts_scr_off = scr;
+    scr = align256(scr + cuts_b);
+    // the superclump rows go out too when they do not fit, or when on the
+    // float path that frees room for the L table beside two CTAs per SM
+    // (each entropy term reads a row and yhat + 1 table entries: one of the two
+    // stays in shared memory)
+    bool sd_out = fixed + reserve > smem_optin;
+    if (!sd_out && fp32 && 2 * (fixed + reserve) > smem_optin + 1024) {
+      const int64_t without = place(false, false);
+      sd_out = 2 * (((without + 15) & ~int64_t(15)) + lbytes + reserve) <= smem_optin + 1024;
+      place(false, true);
+    }
+    if (sd_out) {
       fixed = place(false, false);
       S.sd_scr_off = scr;
       scr = align256(scr + sdbytes);
@@ -158,7 +173,16 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
     S.off_R = (int)o;
     o = (o + rbytes + 15) & ~int64_t(15);
   } else {
-    S.off_L = -1;
+    // the R table is in global memory; the L table still goes to shared
+    // memory when that keeps two CTAs per SM (one for double values)
+    const int64_t with_L = ((o + 15) & ~int64_t(15)) + lbytes;
+    const int ctas = fp32 ? 2 : 1;
+    if (ctas * (with_L + reserve) <= smem_optin + 1024) {
+      S.off_L = (int)((o + 15) & ~int64_t(15));
+      o = (with_L + 15) & ~int64_t(15);
+    } else {
+      S.off_L = -1;
+    }
     S.off_R = -1;
   }
   S.total = (int)o;

@@ -299,6 +299,7 @@ struct DPPlan {
   int64_t sd_scr_off;  // off_sd < 0: the superclump rows live in the CTA's global scratch here
   int64_t x_scr_off;   // off_X < 0: the X buffers live in the CTA's global scratch here
   int off_tb;          // traceback scratch (cuts, I(l), l*(l)): the X region, or its own
+  int64_t cuts_scr_off;  // >= 0: the traceback's path buffers in the CTA's global scratch here
   int64_t scr_bytes;   // global scratch per CTA (0 when the R table is in shared memory)
   int off_I_rel, off_lst_rel;  // within the traceback scratch
   int LS;     // row stride of the R table: source levels 1..lmax-1, mult. of 4

@@ -442,8 +442,10 @@ k_dp(DPParams P, DPPlan S) {
   real* Rtop = reinterpret_cast<real*>(sm + S.off_Rtop);  // R(k, lmax)
   // [2][32][LX] bits: shared memory, or (many levels in double) the CTA's
   // global scratch
-  U* Xb = S.off_X >= 0 ? reinterpret_cast<U*>(sm + S.off_X)
-                       : reinterpret_cast<U*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.x_scr_off);
+  // (with the R table in shared memory they always are: RSM keeps the
+  // pointer a shared-memory one at compile time)
+  U* Xb = (RSM || S.off_X >= 0) ? reinterpret_cast<U*>(sm + S.off_X)
+                                : reinterpret_cast<U*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.x_scr_off);
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);  // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
@@ -453,7 +455,9 @@ k_dp(DPParams P, DPPlan S) {
                 : reinterpret_cast<int*>(sm + S.off_sd);
   // after the DP the traceback scratch (aliased on the X buffers when they
   // are in shared memory)
-  int* cuts = reinterpret_cast<int*>(sm + S.off_tb);                      // [8 NW or NW][xmax]
+  int* cuts = (!RSM && S.cuts_scr_off >= 0)                               // [8 NW or NW][xmax]
+                  ? reinterpret_cast<int*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.cuts_scr_off)
+                  : reinterpret_cast<int*>(sm + S.off_tb);
   double* Iw = reinterpret_cast<double*>(sm + S.off_tb + S.off_I_rel);    // [xmax+1]
   const int LS = S.LS;
   const int LX = S.LX;
@@ -461,7 +465,10 @@ k_dp(DPParams P, DPPlan S) {
   {
     const real* Lsrc;
     if constexpr (fp32) Lsrc = P.L32; else Lsrc = P.L64;
-    if constexpr (RSM) {
+    // in shared memory with the R table (known at compile time, so the
+    // lookups are shared-memory loads); beside a global R table, in shared
+    // memory when the plan has room for it
+    if (RSM || S.off_L >= 0) {
       real* Ls = reinterpret_cast<real*>(sm + S.off_L);
       for (int m = tid; m <= P.n_full; m += T) Ls[m] = Lsrc[m];
       Lt = Ls;
