@@ -485,7 +485,7 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
       if (!(fp32 && g.yhi <= 15 && dp_warp_supported(g.lev, 16))) return GMINE_OK;
       const int tdw = ((g.yhi + 1 + 3) & ~3) <= 8 ? 8 : 16;
       int best = 0;
-      for (int w : {4, 2, 1}) {
+      for (int w : {7, 4, 2, 1}) {
         if (threads > 0 && 32 * w != threads) continue;
         const WarpPlan wp = make_warp_plan((int)n, tg, g.lev, w);
         if (wp.total + 1024 > dev.smem_optin) continue;
@@ -1012,6 +1012,11 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
       pctas = (int)std::min<int64_t>(pctas, cm.partscr_bytes / Q.gscr_per_cta);
       if (!Q.gscr || pctas < 1) return GMINE_E_WORKSPACE;
     }
+    // fewer (pair, orientation) jobs than twice the resident CTAs (few
+    // pairs of many samples): each job's row counts are split over several
+    // CTAs, interleaved
+    Q.parts = (int)std::max<int64_t>(1, std::min<int64_t>(
+        std::min<int64_t>(16, std::max(cp.tb.R, 1)), (2LL * pctas + 2 * C - 1) / (2 * C)));
     GM_CUDA(cudaMemsetAsync(Q.queue, 0, 8, st));
     GM_CUDA(partition_launch(cp.part_global, cp.part_wide, pctas, 32 * cp.part.warps,
                              cp.part_global ? 0 : cp.part.total, st, Q));

@@ -234,7 +234,8 @@ struct PartParams {
   double c;
   int64_t chunk_pairs;
   const int64_t* rec_off;     // [B/2+2] first int of row count y's record
-  unsigned long long* queue;  // atomic (pair, orientation) counter
+  unsigned long long* queue;  // atomic job counter: (part, pair, orientation)
+  int parts;                  // CTAs per (pair, orientation), row counts interleaved
   int off_pi, off_gU;  // shared by the CTA: [n] uint16 each
   int off_warps;       // first per-warp region
   int warp_smem;       // bytes of shared memory per warp

@@ -59,7 +59,7 @@ __device__ __forceinline__ float entropy_w(const float* __restrict__ Lt, const i
 }  // namespace
 
 template <int LEV, int TDW>
-__global__ void __launch_bounds__(128, 4) k_dp_warp(DPParams P, WarpPlan S) {
+__global__ void __launch_bounds__(224, 2) k_dp_warp(DPParams P, WarpPlan S) {
   using BT = Bits<float>;
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31;

@@ -51,19 +51,24 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
   for (;;) {
     if (threadIdx.x == 0) {
       s_job = (long long)atomicAdd(P.queue, 1ull);
-      s_y = 2;
+      s_y = 0;
     }
     __syncthreads();
     const int64_t job = s_job;
     __syncthreads();
-    if (job >= 2 * C) break;
-    const int64_t pl = job >> 1;
-    const int o = (int)(job & 1);
+    // job = part * 2C + (pair * 2 + o): with P.parts > 1 several CTAs share a
+    // (pair, o), part j taking the row counts y = 2 + j, 2 + j + parts, ...
+    // (the first parts, with the heavy small y, come first)
+    if (job >= 2 * C * P.parts) break;
+    const int part = (int)(job / (2 * C));
+    const int64_t pj = job - (int64_t)part * 2 * C;
+    const int64_t pl = pj >> 1;
+    const int o = (int)(pj & 1);
     const int n = P.pp.n_used[pl];
     const int B = P.pp.B[pl];
     int32_t* rec0 = P.rec + ((int64_t)pl * 2 + o) * P.rec_per_orient;
     if (n < 4 || B < 4) {
-      for (int y = 2 + (int)threadIdx.x; y <= P.B_full / 2; y += blockDim.x) {
+      for (int y = 2 + part + P.parts * (int)threadIdx.x; y <= P.B_full / 2; y += P.parts * blockDim.x) {
         int32_t* rec = rec0 + P.rec_off[y];
         rec[0] = 0;
         rec[1] = 0;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
     // the small y first) by whichever warp is free
     for (;;) {
       int yy = 0;
-      if (lane == 0) yy = atomicAdd(&s_y, 1);
+      if (lane == 0) yy = 2 + part + P.parts * atomicAdd(&s_y, 1);
       const int y = __shfl_sync(0xffffffffu, yy, 0);
       if (y > P.B_full / 2) break;
       int32_t* rec = rec0 + P.rec_off[y];
