@@ -405,6 +405,7 @@ def main():
     launches = 0
     dp_launches = 0
     elapsed = 0.0
+    stage_ms = dict.fromkeys(gmine.STAGE_NAMES, 0.0)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
@@ -412,6 +413,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
         elapsed += e0.elapsed_time(e1)
+        for k, v in meas.stage_ms.items():
+            stage_ms[k] += v
         dp_ms += meas.dp_ms
         dp_launches += meas.dp_launches
         launches += meas.kernel_launches
@@ -421,6 +424,11 @@ def main():
     clk = clocks.stop()
     ms_step = elapsed / args.steps
     ms_step_max = max_over_ranks(ms_step, dist, dev)
+    # where a step's time goes: the call's stages (CUDA events between them,
+    # summed over chunks) and the rest of the step (host work between chunks
+    # that the GPU waited for, launch gaps)
+    breakdown = {k: v / args.steps for k, v in stage_ms.items()}
+    breakdown["outside_stages"] = ms_step - sum(breakdown.values())
     value = world * npairs / (ms_step_max / 1e3)
 
     # the plain FP64 DP on all pairs of the first fp64_vars variables: one
@@ -607,6 +615,7 @@ def main():
                          "dp_kernel_ms_per_step": dp_ms / args.steps,
                          "dp_launches_per_step": dp_launches // args.steps,
                          "tasks_per_step": tasks // args.steps},
+            "step_breakdown_ms": breakdown,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,

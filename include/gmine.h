@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define GMINE_ABI_VERSION 2
+#define GMINE_ABI_VERSION 3
 
 /* status codes */
 #define GMINE_OK 0
@@ -70,6 +70,9 @@ extern "C" {
 #define GMINE_E_CUDA 7       /* a CUDA runtime call failed */
 #define GMINE_E_LIMIT 8      /* a size beyond what this build supports (n > 131072) */
 #define GMINE_E_NODEVICE 9   /* no usable CUDA device */
+#define GMINE_E_TIMEOUT 10   /* pair: a bounded wait between the warps of a
+                                kernel ran out; the pair's results are not
+                                valid (not expected: a safety bound) */
 
 /* precision of the OptimizeXAxis dynamic program */
 #define GMINE_PLAIN_FP64 0            /* entropies and DP in double */
@@ -134,7 +137,27 @@ typedef struct {
                              launch_cap of them                            */
     int32_t launch_cap;
     int32_t reserved2;
+    double *h_stage_ms;   /* host: if not NULL, [GMINE_N_STAGES] milliseconds
+                             of each stage of the call (GMINE_STAGE_*), summed
+                             over chunks, from CUDA events recorded on
+                             `stream` between the stages; the stream is
+                             synchronised before returning.  The call's
+                             stream time outside these intervals (host work
+                             between chunks, event gaps) is in none.      */
 } gmine_trace;
+
+/* Stages of a batch call, indexes of gmine_trace.h_stage_ms. */
+#define GMINE_STAGE_SETUP 0      /* per-variable preparation: non-finite counts,
+                                    ranks, equipartitions, L and log tables;
+                                    for uneven batches the pair sizes and the
+                                    chunk tables */
+#define GMINE_STAGE_PAIRS 1      /* per chunk: pair slots and per-pair ranks */
+#define GMINE_STAGE_EQUI 2       /* per chunk: per-pair equipartitions */
+#define GMINE_STAGE_PARTITION 3  /* per chunk: clumps, superclumps, count
+                                    tables of every task */
+#define GMINE_STAGE_DP 4         /* per chunk: the OptimizeXAxis launches */
+#define GMINE_STAGE_FINAL 5      /* per chunk: M and the statistics */
+#define GMINE_N_STAGES 6
 
 /* ---- parameters, errors ------------------------------------------------ */
 
@@ -266,7 +289,8 @@ int gmine_plan_uneven(int64_t p, int64_t n, int64_t n_pairs, const double *h_alp
      gmine_compute_batch: pair i's score at i, its cells at i *
      m_cells_per_pair.
    - trace: NULL, or only the counters and timing fields set (d_counters,
-     h_dp_ms, h_dp_launches, h_kernel_launches); per-task arrays are refused.
+     h_dp_ms, h_dp_launches, h_kernel_launches, h_launch_ms, h_stage_ms);
+     per-task arrays are refused.
    How it runs: the pairs' alpha indices and sample counts are read back to
    the host (the call synchronises `stream` twice), the pairs are ordered by
    their DP work, heaviest first, and cut into chunks that fit the

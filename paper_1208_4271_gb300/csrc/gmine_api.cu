@@ -99,6 +99,7 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   const int rs = fp32 ? 4 : 8;
   const int NW = threads / 32;
   DPPlan S{};
+  S.off_Eb2 = -1;
   S.LS = std::max(4, (tb.lmax - 1 + 3) & ~3);
   S.LX = std::max(4, (tb.lmax + 3) & ~3) | 1;
   S.xmax = std::max(tb.xmax, 2);
@@ -390,6 +391,35 @@ struct DPTiming {
   }
 };
 
+// CUDA events between the stages of one call (h_stage_ms of gmine_trace):
+// mark(s) closes stage s, begun at the previous mark; s < 0 only starts.
+struct StageTiming {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> stage;
+  ~StageTiming() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  cudaError_t mark(int s, cudaStream_t st) {
+    cudaEvent_t e;
+    const cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    stage.push_back(s);
+    return cudaEventRecord(e, st);
+  }
+  cudaError_t sums(double* out) const {
+    for (int s = 0; s < GMINE_N_STAGES; ++s) out[s] = 0.0;
+    for (size_t i = 1; i < ev.size(); ++i) {
+      if (stage[i] < 0) continue;
+      float ms = 0.f;
+      const cudaError_t r = cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      if (r != cudaSuccess) return r;
+      out[stage[i]] += ms;
+    }
+    return cudaSuccess;
+  }
+};
+
 // Tuned DP choices (gmine_set_dp_choices): per batch shape (n, B, c,
 // precision) the kernel shape and CTA size of launch groups, process-wide.
 struct ChoiceSet {
@@ -563,6 +593,20 @@ int plan_chunk(int64_t n, int B, double c, bool fp32, const DeviceInfo& dev, Chu
         }
       }
       if (best_warps <= 0) return GMINE_OK;
+      // a second in-block triangle when it costs no resident CTA: the next
+      // block's then needs no wait for warp 0
+      {
+        DPPlan S2 = g.S;
+        S2.off_Eb2 = (S2.total + 15) & ~15;
+        S2.total = (int)((S2.off_Eb2 + (int64_t)(32 * 31 / 2) * (fp32 ? 4 : 8) + 15) & ~int64_t(15));
+        if (S2.total <= dev.smem_optin) {
+          int b1 = 0, b2 = 0;
+          int r = dp_occupancy(fp32, g.rsm, g.lev, std::max(g.S.total, 1), g.threads, &b1);
+          if (r == GMINE_OK) r = dp_occupancy(fp32, g.rsm, g.lev, S2.total, g.threads, &b2);
+          if (r != GMINE_OK) return r;
+          if (b2 >= b1) g.S = S2;
+        }
+      }
       // the launch attribute must allow the chosen plan (the loop left the
       // last candidate's size in place)
       int blocks = 0;
@@ -938,6 +982,7 @@ struct BatchCtx {
   int64_t m_stride;
   const gmine_trace* trace;
   DPTiming* timing;
+  StageTiming* stages;
   cudaStream_t st;
   int launches;
 };
@@ -949,6 +994,8 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
   const Layout& L = *b.L;
   cudaStream_t st = b.st;
   PairPrep pp = cm.pp;
+  auto mark = [&](int s) -> cudaError_t { return b.stages ? b.stages->mark(s, st) : cudaSuccess; };
+  GM_CUDA(mark(-1));
   GM_CUDA(cudaMemsetAsync(pp.ndirty, 0, 4, st));
   k_pair_prep<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(b.pairs, pair0, C, b.p, (int)b.n_row,
                                                             b.nf, b.Btab, pp);
@@ -969,6 +1016,7 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
                         cp.rank_scr_per_cta));
     ++b.launches;
   }
+  GM_CUDA(mark(GMINE_STAGE_PAIRS));
   if (cp.tb.R > 0) {
     const int64_t work = 2 * C * cp.tb.R;
     k_equi<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(pp.slot0, 2 * C, pp.slot0, b.Btab_slots,
@@ -976,6 +1024,7 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
     GM_CUDA(cudaGetLastError());
     ++b.launches;
   }
+  GM_CUDA(mark(GMINE_STAGE_EQUI));
   const int64_t ntasks = 2 * (int64_t)cp.tb.R * C;
   if (ntasks > 0) {
     // partition of every task of the chunk
@@ -1022,6 +1071,7 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
                              cp.part_global ? 0 : cp.part.total, st, Q));
     GM_CUDA(cudaGetLastError());
     ++b.launches;
+    GM_CUDA(mark(GMINE_STAGE_PARTITION));
     // the dynamic program: large row counts... small row counts
     DPParams P{};
     P.pp = pp;
@@ -1078,6 +1128,7 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
       ++b.launches;
       if (b.timing) GM_CUDA(cudaEventRecord(e1, st));
     }
+    GM_CUDA(mark(GMINE_STAGE_DP));
   }
   FinalParams F{};
   F.Mo = cm.Mo;
@@ -1093,12 +1144,17 @@ int run_chunk(BatchCtx& b, const ChunkPlan& cp, const ChunkMem& cm, int64_t pair
   k_final<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(F);
   GM_CUDA(cudaGetLastError());
   ++b.launches;
+  GM_CUDA(mark(GMINE_STAGE_FINAL));
   return GMINE_OK;
 }
 
 // The trace epilogue of a batch call: launch count and DP kernel time.
 int finish_trace(const BatchCtx& b) {
   if (b.trace && b.trace->h_kernel_launches) *b.trace->h_kernel_launches = b.launches;
+  if (b.stages) {
+    GM_CUDA(cudaStreamSynchronize(b.st));
+    GM_CUDA(b.stages->sums(b.trace->h_stage_ms));
+  }
   if (b.timing) {
     GM_CUDA(cudaStreamSynchronize(b.st));
     double ms = 0.0;
@@ -1313,6 +1369,7 @@ const char* gmine_strerror(int status) {
     case GMINE_E_CUDA: return cudaGetErrorString(last_cuda_error());
     case GMINE_E_LIMIT: return "size beyond the limits of this build";
     case GMINE_E_NODEVICE: return "no usable CUDA device";
+    case GMINE_E_TIMEOUT: return "a bounded wait inside a kernel ran out";
     default: return "unknown status";
   }
 }
@@ -1391,8 +1448,12 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* ws = d_workspace;
   int launches = 0;
+  StageTiming stg;
+  StageTiming* stages = (trace && trace->h_stage_ms) ? &stg : nullptr;
+  if (stages) GM_CUDA(stages->mark(-1, st));
   rc = prepare_variables(d_vars, ws, L, param->alpha, param->c, st, &launches);
   if (rc != GMINE_OK) return rc;
+  if (stages) GM_CUDA(stages->mark(GMINE_STAGE_SETUP, st));
   if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
   DPTiming tim;
   BatchCtx b{};
@@ -1413,6 +1474,7 @@ int gmine_compute_batch_ex(const double* d_vars, int64_t p, int64_t n, const int
   b.m_stride = L.cp.cells;
   b.trace = trace;
   b.timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
+  b.stages = stages;
   b.st = st;
   b.launches = launches;
   const ChunkMem cm = regular_mem(ws, L);
@@ -1474,6 +1536,9 @@ int gmine_compute_batch_uneven(const double* d_vars, int64_t p, int64_t n, const
     for (uint8_t a : ai)
       if (a >= n_alphas) return GMINE_E_ARG;
   }
+  StageTiming stg;
+  StageTiming* stages = (trace && trace->h_stage_ms) ? &stg : nullptr;
+  if (stages) GM_CUDA(stages->mark(-1, st));
   rc = upload_Btab(ws, L, h_alphas, n_alphas, st);
   if (rc != GMINE_OK) return rc;
   int launches = 0;
@@ -1500,6 +1565,7 @@ int gmine_compute_batch_uneven(const double* d_vars, int64_t p, int64_t n, const
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
   GM_CUDA(cudaMemcpyAsync(at<int32_t>(ws, L.o_order), order.data(), sizeof(int32_t) * order.size(),
                           cudaMemcpyHostToDevice, st));
+  if (stages) GM_CUDA(stages->mark(GMINE_STAGE_SETUP, st));
   if (trace && trace->d_counters) GM_CUDA(cudaMemsetAsync(trace->d_counters, 0, 16, st));
   DPTiming tim;
   BatchCtx b{};
@@ -1520,6 +1586,7 @@ int gmine_compute_batch_uneven(const double* d_vars, int64_t p, int64_t n, const
   b.m_stride = L.cp.cells;
   b.trace = trace;
   b.timing = (trace && trace->h_dp_ms) ? &tim : nullptr;
+  b.stages = stages;
   b.st = st;
   b.launches = launches;
   int64_t i = 0;
@@ -1546,9 +1613,11 @@ int gmine_compute_batch_uneven(const double* d_vars, int64_t p, int64_t n, const
     if (rc != GMINE_OK) return rc;
     ChunkMem cm = uneven_mem(ws, L, j - i, nc, Bc);
     cm.pp.aidx = d_alpha_idx;
+    if (stages) GM_CUDA(stages->mark(-1, st));
     k_tables<<<1, 256, 0, st>>>(-1, nullptr, nullptr, nullptr, Bc, (int)nc, c, cm.rec_off);
     GM_CUDA(cudaGetLastError());
     ++b.launches;
+    if (stages) GM_CUDA(stages->mark(GMINE_STAGE_SETUP, st));
     rc = run_chunk(b, cp, cm, i, j - i);
     if (rc != GMINE_OK) return rc;
     i = j;

@@ -297,6 +297,7 @@ struct MidPlan {
 // Shared-memory layout of the DP kernel (byte offsets).
 struct DPPlan {
   int off_R, off_Rtop, off_X, off_Eb, off_rbuf, off_L, off_sd;
+  int off_Eb2;  // a second in-block triangle (double buffering), or -1
   int64_t sd_scr_off;  // off_sd < 0: the superclump rows live in the CTA's global scratch here
   int64_t x_scr_off;   // off_X < 0: the X buffers live in the CTA's global scratch here
   int off_tb;          // traceback scratch (cuts, I(l), l*(l)): the X region, or its own

@@ -19,14 +19,17 @@
 //   A1: s below block b  (rows final before block b is solved),
 //   A2: s inside block b (rows final once block b is solved),
 //   B:  s inside block b+1 itself, one t after another.
-// Warp 0 solves block b (its part B) while the other warps work through A1
-// of block b+1, taking s-chunks from a shared counter (warp 0 joins when it
-// is done); then all warps do A2.  In A1/A2 each lane computes E(s,t) once
-// and updates the running maxima of a group of levels with R(s,l-1) - E
-// (the R row is a warp-wide 16-byte broadcast); the warps' partial maxima
-// meet in shared memory through atomicMin on the value bits (every value is
-// -0.0, negative or -inf, so a larger value has smaller bits).  Levels
-// beyond a task's last level hold -inf, so no candidate needs a guard.
+// Warp 0 solves block b (its part B) while the other warps work through the
+// items of block b+1 from a shared counter: the A1 s-chunks, the entries of
+// block b+1's in-block entropy triangle (once warp 0 holds block b's in
+// registers), then the A2 s-chunks, which wait for warp 0 to publish block
+// b's rows; warp 0 joins when it is done, and one barrier per block ends the
+// step.  In A1/A2 each lane computes E(s,t) once and updates the running
+// maxima of a group of levels with R(s,l-1) - E (the R row is a warp-wide
+// 16-byte broadcast); the warps' partial maxima meet in shared memory
+// through atomicMin on the value bits (every value is -0.0, negative or
+// -inf, so a larger value has smaller bits).  Levels beyond a task's last
+// level hold -inf, so no candidate needs a guard.
 #pragma once
 #include "gmine_internal.cuh"
 #include "kernels.h"
@@ -244,20 +247,77 @@ __device__ __forceinline__ void flush(const real (&acc)[LEV], typename Bits<real
     if (lc + i <= lmax) atomicMin(&Xrow[lc + i - 1], BT::of(acc[i]));
 }
 
-// Phase A over the s range [s_begin, s_end) of one part (A1 with a shared
-// work counter, or A2 with a static split), LEV levels per pass.
+// Iterations of a bounded wait (under a tenth of a second with the sleep in
+// each); a wait that runs out marks the task's pair GMINE_E_TIMEOUT, and the
+// task's later waits return at once.  (Warp 0 publishes each block after its
+// in-block step, which waits on nothing: the bound is a safety net.)
+constexpr unsigned kWaitLimit = 1u << 20;
+
+// Lane 0 waits until *ready >= want (warp 0 stores the number of blocks
+// whose R rows are final after a block-scope fence), then the warp goes on.
+__device__ __forceinline__ void wait_ready(const int* ready, int want, int lane, bool& late) {
+  if (lane == 0 && !late) {
+    const volatile int* r = ready;
+    unsigned it = 0;
+    while (*r < want) {
+      if (++it > kWaitLimit) {
+        late = true;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence_block();
+  }
+  __syncwarp();
+}
+
+// Entries of the in-block entropy triangle of the block starting at t0:
+// E(t0+i, t0+j), 0 <= i < j <= 31, at j(j-1)/2 + i (those with t0+j <= k).
+constexpr int kEbEntries = 32 * 31 / 2;
+__device__ __forceinline__ int tri_column(int p) {  // j with j(j-1)/2 <= p < j(j+1)/2
+  int j = (int)((1.0f + sqrtf(8.0f * (float)p + 1.0f)) * 0.5f);
+  while (j * (j - 1) / 2 > p) --j;
+  while (j * (j + 1) / 2 <= p) ++j;
+  return j;
+}
+template <typename real>
+__device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const real* __restrict__ Lt,
+                                                   const int* __restrict__ sd, int SW, int yhat, int t0,
+                                                   int k, int u, int U) {
+  for (int p = u; p < kEbEntries; p += U) {
+    const int j = tri_column(p);
+    if (t0 + j <= k) Eb[p] = entropy_term<real>(Lt, sd, SW, yhat, t0 + (p - j * (j - 1) / 2), t0 + j);
+  }
+}
+
+// The work for block b+1 (t in [t1, t1 + 32)) while warp 0 solves block b,
+// in items from one shared counter, LEV levels per pass:
+//   A1 s-chunks of 16, s in [1, t0) (rows final before block b);
+//   block b+1's in-block triangle, 32 entries per item, into EbN (a buffer
+//   of its own, or, with eb_wait, block b's once warp 0 holds that in
+//   registers: *ebfree >= want);
+//   A2 s-chunks of 32/NW (at least 4), s in block b [t0, t1): these wait
+//   until warp 0 has published block b's rows (*ready >= want).
+// The A items of a pass share the running maxima, flushed into the X rows of
+// block b+1 by atomicMin on the value bits when the pass changes.
 template <typename real, int LEV>
-__device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int lmax, int s_begin, int s_end,
-                        bool stealing, int* s_next, const real* __restrict__ Lt,
-                        const int* __restrict__ sd, int SW, int yhat,
-                        int tt, bool tv, typename Bits<real>::U* Xrow, int warp, int NW, int lane) {
+__device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS, int lmax, int t0,
+                                            int t1, int k, int* cnt, const int* ready,
+                                            const int* ebfree, int want,
+                                            const real* __restrict__ Lt, const int* __restrict__ sd,
+                                            int SW, int yhat, int tt, bool tv,
+                                            typename Bits<real>::U* Xrow, real* __restrict__ EbN,
+                                            bool eb_wait, int NW, int lane, bool& late) {
   using BT = Bits<real>;
   constexpr bool fp32 = sizeof(real) == 4;
-  const int CH = stealing ? 16 : 4;  // s per grab
+  constexpr int nT = (kEbEntries + 31) / 32;
   const int nlev = lmax - 1;
   const int npass = (nlev + LEV - 1) / LEV;
-  const int nsb = (s_end - s_begin + CH - 1) / CH;  // s-chunks per pass
-  if (nsb <= 0) return;
+  const int nsb1 = (t0 - 1 + 15) / 16;
+  const int nA1 = npass * nsb1;
+  const int n2 = min(NW, 8);  // A2 items per pass
+  const int ch2 = 32 / n2;
+  const int total = nA1 + nT + npass * n2;
   // this lane's row t in registers when it is short
   const bool reg = yhat <= 7;
   int td[8];
@@ -265,24 +325,45 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
   for (int c = 0; c < 8; ++c) td[c] = (reg && c < SW) ? sd[tt * SW + c] : 0;
   real acc[LEV];
   int cur_pass = -1;
-  int g = stealing ? 0 : warp;
+  bool waited = false, waited_eb = false;
   for (;;) {
-    if (stealing) {
-      int gg = 0;
-      if (lane == 0) gg = atomicAdd(s_next, 1);
-      g = __shfl_sync(0xffffffffu, gg, 0);
+    int gg = 0;
+    if (lane == 0) gg = atomicAdd(cnt, 1);
+    const int g = __shfl_sync(0xffffffffu, gg, 0);
+    if (g >= total) break;
+    int pass, s_lo, s_hi;
+    if (g < nA1) {
+      pass = g / nsb1;
+      s_lo = 1 + (g - pass * nsb1) * 16;
+      s_hi = min(t0 - 1, s_lo + 15);
+    } else if (g < nA1 + nT) {
+      if (eb_wait && !waited_eb) {
+        wait_ready(ebfree, want, lane, late);
+        waited_eb = true;
+      }
+      const int p = (g - nA1) * 32 + lane;
+      if (p < kEbEntries) {
+        const int j = tri_column(p);
+        if (t1 + j <= k)
+          EbN[p] = entropy_term<real>(Lt, sd, SW, yhat, t1 + (p - j * (j - 1) / 2), t1 + j);
+      }
+      continue;
+    } else {
+      const int h = g - nA1 - nT;
+      pass = h / n2;
+      s_lo = t0 + (h - pass * n2) * ch2;
+      s_hi = s_lo + ch2 - 1;
+      if (!waited) {
+        wait_ready(ready, want, lane, late);
+        waited = true;
+      }
     }
-    if (g >= nsb * npass) break;
-    const int pass = g / nsb;
-    const int sb = g - pass * nsb;
     if (pass != cur_pass) {
       if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
 #pragma unroll
       for (int i = 0; i < LEV; ++i) acc[i] = BT::ninf();
       cur_pass = pass;
     }
-    const int s_lo = s_begin + sb * CH;
-    const int s_hi = min(s_end - 1, s_lo + CH - 1);
     // float: the row width's fixed number of terms, no branch on yhat; double:
     // only yhat terms (the padding terms would cost FP64 issue slots)
     if (reg && fp32 && SW == 4)
@@ -293,7 +374,6 @@ __device__ __forceinline__ void phase_a(const real* __restrict__ Rt, int LS, int
       accumulate<real, LEV, 1>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
     else
       accumulate<real, LEV, 0>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
-    if (!stealing) g += NW;
   }
   if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
 }
@@ -310,34 +390,6 @@ __host__ __device__ __forceinline__ int level_group(int nlev) {
   return 40;
 }
 
-// Named barrier 1 (barrier 0 is __syncthreads): warp 0 arrives once it has
-// read the in-block triangle, the other warps wait there before they
-// overwrite it; nthreads = the CTA's threads, all of them take part.
-__device__ __forceinline__ void bar_arrive(int id, int nthreads) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void bar_wait(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Entries of the in-block entropy triangle of the block starting at t0:
-// E(t0+i, t0+j), 0 <= i < j <= 31, at j(j-1)/2 + i (those with t0+j <= k),
-// entry p by thread u, u + U, ...
-constexpr int kEbEntries = 32 * 31 / 2;
-template <typename real>
-__device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const real* __restrict__ Lt,
-                                                   const int* __restrict__ sd, int SW, int yhat, int t0,
-                                                   int k, int u, int U) {
-  int j = 1, base = 0;  // base = j(j-1)/2
-  for (int p = u; p < kEbEntries; p += U) {
-    while (base + j <= p) {
-      base += j;
-      ++j;
-    }
-    if (t0 + j <= k) Eb[p] = entropy_term<real>(Lt, sd, SW, yhat, t0 + (p - base), t0 + j);
-  }
-}
-
 // The candidates of block b with s inside the block, level after level:
 // lane j owns t0+j and keeps the column E(t0+i, t0+j), i < j, in registers
 // (+inf for i >= j, so those candidates are -inf).  At level l the 32
@@ -351,7 +403,8 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
                                               int LX, int lmax, int t0, int k,
                                               const typename Bits<real>::U* __restrict__ Xcur,
                                               bool has_x, const real* __restrict__ Eb,
-                                              real* __restrict__ rbuf, int lane, int release_T) {
+                                              real* __restrict__ rbuf, int lane,
+                                              int* ebfree, int eb_val) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   const int t = t0 + lane;
@@ -362,10 +415,14 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
   real ec[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) ec[i] = (tv && i < lane) ? Eb[lane * (lane - 1) / 2 + i] : pinf;
-  if (release_T > 0) {
-    // the triangle is in registers: the other warps may overwrite it
+  // the triangle is in registers: the next block's may overwrite it (with
+  // a single triangle buffer)
+  if (ebfree) {
     __syncwarp();
-    bar_arrive(1, release_T);
+    if (lane == 0) {
+      __threadfence_block();
+      *reinterpret_cast<volatile int*>(ebfree) = eb_val;
+    }
   }
   real rcur = tv ? Rt[t * LS] : BT::ninf();  // level 1
   const typename Bits<real>::U* xr = Xcur + lane * LX;
@@ -425,7 +482,9 @@ k_dp(DPParams P, DPPlan S) {
   using U = typename BT::U;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_task;
-  __shared__ int s_next;
+  __shared__ int s_cnt[2];  // work counters of the block steps, by parity
+  __shared__ int s_ready;   // blocks whose R rows are final
+  __shared__ int s_ebfree;  // blocks whose triangle warp 0 holds in registers
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int lane = tid & 31;
@@ -446,7 +505,11 @@ k_dp(DPParams P, DPPlan S) {
   // pointer a shared-memory one at compile time)
   U* Xb = (RSM || S.off_X >= 0) ? reinterpret_cast<U*>(sm + S.off_X)
                                 : reinterpret_cast<U*>(P.scratch + (int64_t)blockIdx.x * P.scratch_per_cta + S.x_scr_off);
-  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);  // E(t0+i, t0+j) at j(j-1)/2 + i, i < j
+  // E(t0+i, t0+j) at j(j-1)/2 + i, i < j: with two buffers block b's in
+  // buffer b % 2; with one, block b's until warp 0 has taken it into
+  // registers, then block b+1's
+  real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);
+  real* Eb2 = S.off_Eb2 >= 0 ? reinterpret_cast<real*>(sm + S.off_Eb2) : Eb;
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
   // the R table in the CTA's scratch
@@ -531,9 +594,15 @@ k_dp(DPParams P, DPPlan S) {
         else if (t == k) *Rtop = r1;
       }
       in_block_entropies<real>(Eb, Lt, sd, SW, yhat, 1, k, tid, T);  // block 0
-      if (tid == 0) s_next = 0;
+      if (tid == 0) {
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_ready = 0;
+        s_ebfree = 0;
+      }
       __syncthreads();
 
+      bool late = false;
       const int nb = (k + 31) / 32;
       for (int b = 0; b < nb; ++b) {
         const int t0 = 1 + 32 * b;
@@ -541,37 +610,32 @@ k_dp(DPParams P, DPPlan S) {
         const bool next = t1 <= k;
         U* Xcur = Xb + (b & 1) * 32 * LX;
         U* Xnxt = Xb + ((b + 1) & 1) * 32 * LX;
-        const int tn = t1 + lane;  // this lane's t in block b+1
-        const bool tnv = next && tn <= k;
-        const int ttn = tnv ? tn : k;
-        // block b+1's in-block triangle replaces block b's while warp 0
-        // solves block b (every thread takes the same branch: next, NW)
-        const bool eb_early = next && NW > 1;
-        for (int step = 0; step < 2; ++step) {
-          if (step == 0 && warp == 0)  // ---- block b, s inside the block
-            phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, Eb, rbuf, lane,
-                                eb_early ? T : 0);
-          if (step == 0 && eb_early && warp > 0) {
-            bar_wait(1, T);
-            in_block_entropies<real>(Eb, Lt, sd, SW, yhat, t1, k, tid - 32, T - 32);
+        if (warp == 0) {
+          // ---- block b, s inside the block
+          phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, (b & 1) ? Eb2 : Eb, rbuf,
+                              lane, Eb2 == Eb ? &s_ebfree : nullptr, b + 1);
+          // block b's X rows are consumed: cleared for block b+2; the other
+          // counter is free until the next step
+          for (int i = lane; i < 32 * LX; i += 32) Xcur[i] = NINF_BITS;
+          if (lane == 0) s_cnt[(b + 1) & 1] = 0;
+          __syncwarp();
+          if (lane == 0) {
+            __threadfence_block();
+            *reinterpret_cast<volatile int*>(&s_ready) = b + 1;
           }
-          // step 0: A1 of block b+1, s in [1, t0 - 1], shared work counter
-          // (warp 0 joins once block b is solved);
-          // step 1: A2 of block b+1, s in block b, static split
-          const bool stealing = step == 0;
-          const int sb0 = stealing ? 1 : t0;
-          const int sb1 = stealing ? t0 : t1;
-          if (next && sb1 > sb0)
-            phase_a<real, LEV>(Rt, LS, lmax, sb0, sb1, stealing, &s_next, Lt, sd, SW, yhat, ttn,
-                               tnv, Xnxt + lane * LX, warp, NW, lane);
-          if (step == 1) {
-            for (int i = tid; i < 32 * LX; i += T) Xcur[i] = NINF_BITS;  // for block b+2
-            if (tid == 0) s_next = 0;
-            if (next && NW == 1) in_block_entropies<real>(Eb, Lt, sd, SW, yhat, t1, k, tid, T);
-          }
-          __syncthreads();
+          __syncwarp();
         }
+        // ---- block b+1: A1, its triangle, A2 (warp 0 joins when done)
+        if (next) {
+          const int tn = t1 + lane;  // this lane's t in block b+1
+          const bool tnv = tn <= k;
+          block_items<real, LEV>(Rt, LS, lmax, t0, t1, k, &s_cnt[b & 1], &s_ready, &s_ebfree, b + 1,
+                                 Lt, sd, SW, yhat, tnv ? tn : k, tnv, Xnxt + lane * LX,
+                                 ((b + 1) & 1) ? Eb2 : Eb, Eb2 == Eb, NW, lane, late);
+        }
+        __syncthreads();
       }
+      if (late) atomicOr(&P.pp.flags[pl], 1 << GMINE_E_TIMEOUT);
     }
 
     // ---- I(l) for l = 2..x

@@ -92,7 +92,9 @@ __global__ void k_final(FinalParams F) {
   sc.mcn = log2((double)mcn_xy);
   sc.mcn_xy = mcn_xy;
   sc.m_cells = cells;
-  sc.status = (flags & (1 << GMINE_E_CONSTANT)) ? GMINE_E_CONSTANT : GMINE_OK;
+  sc.status = (flags & (1 << GMINE_E_TIMEOUT))    ? GMINE_E_TIMEOUT
+              : (flags & (1 << GMINE_E_CONSTANT)) ? GMINE_E_CONSTANT
+                                                  : GMINE_OK;
   if (lane == 0) F.scores[pi] = sc;
 }
 

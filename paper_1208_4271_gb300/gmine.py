@@ -12,7 +12,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmine.so")
 
-OK, E_PARAM, E_TOO_FEW, E_CONSTANT, E_NOMEM, E_ARG, E_WORKSPACE, E_CUDA, E_LIMIT, E_NODEVICE = range(10)
+(OK, E_PARAM, E_TOO_FEW, E_CONSTANT, E_NOMEM, E_ARG, E_WORKSPACE, E_CUDA, E_LIMIT, E_NODEVICE,
+ E_TIMEOUT) = range(11)
 PLAIN_FP64 = 0
 FP32_DP_FP64_RESCORE = 1
 PLAN_HOST_STAGING = 1
@@ -44,7 +45,11 @@ class Trace(ctypes.Structure):
                 ("d_counters", ctypes.c_void_p), ("h_dp_ms", ctypes.c_void_p),
                 ("h_dp_launches", ctypes.c_void_p), ("h_kernel_launches", ctypes.c_void_p),
                 ("h_launch_ms", ctypes.c_void_p), ("launch_cap", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("reserved2", ctypes.c_int32), ("h_stage_ms", ctypes.c_void_p)]
+
+
+N_STAGES = 6
+STAGE_NAMES = ("setup", "pairs", "equi", "partition", "dp", "final")
 
 
 DP_BLOCKED, DP_WARP, DP_MID, DP_SMALL, DP_TWO = range(5)
@@ -201,7 +206,8 @@ class Measure:
     """Counters and DP kernel timing of one batch call (gmine_trace without
     the per-task tables): subtract-and-max steps, tasks, summed DP kernel
     milliseconds measured with CUDA events on the call's stream, and the
-    milliseconds of each DP launch (up to launch_cap)."""
+    milliseconds of each DP launch (up to launch_cap) and of each stage of
+    the call (stage_ms)."""
 
     def __init__(self, device="cuda", launch_cap=4096):
         import torch
@@ -210,11 +216,18 @@ class Measure:
         self._launches = ctypes.c_int32(0)
         self._kernels = ctypes.c_int32(0)
         self._launch_ms = np.zeros(launch_cap, dtype=np.float32)
+        self._stage_ms = np.zeros(N_STAGES, dtype=np.float64)
         self.trace = Trace(None, None, None, None, 0, 0, None, None, 0, 0,
                            _dptr(self.counters), ctypes.cast(ctypes.byref(self._ms), ctypes.c_void_p),
                            ctypes.cast(ctypes.byref(self._launches), ctypes.c_void_p),
                            ctypes.cast(ctypes.byref(self._kernels), ctypes.c_void_p),
-                           self._launch_ms.ctypes.data_as(ctypes.c_void_p), launch_cap, 0)
+                           self._launch_ms.ctypes.data_as(ctypes.c_void_p), launch_cap, 0,
+                           self._stage_ms.ctypes.data_as(ctypes.c_void_p))
+
+    @property
+    def stage_ms(self):
+        """Milliseconds of each stage of the last call (STAGE_NAMES order)."""
+        return dict(zip(STAGE_NAMES, (float(v) for v in self._stage_ms)))
 
     @property
     def launch_ms(self):

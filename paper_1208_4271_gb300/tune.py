@@ -42,7 +42,7 @@ def candidates(group, B, fp32):
         out += [(gmine.DP_TWO, t) for t in (64, 128, 256)]
     out += [(gmine.DP_BLOCKED, t) for t in (128, 256)]
     if fp32 and group["yhi"] <= 15:
-        out += [(gmine.DP_WARP, t) for t in (32, 64, 128)]
+        out += [(gmine.DP_WARP, t) for t in (32, 64, 128, 224)]
     out += [(gmine.DP_MID, t) for t in (128, 256)]
     if x_lo <= 9:
         out += [(gmine.DP_SMALL, t) for t in (32, 64, 128)]
@@ -167,7 +167,9 @@ def save(entry, path=None):
 
 def apply(entries=None, device_name=None, setter=None):
     """Hand the cached choices of this device to the library; returns how
-    many shapes were applied."""
+    many shapes were applied.  A group whose measured best was the planner's
+    own choice at tuning time is left to the planner's rules (which may have
+    improved since); only the choices that beat the rules are handed over."""
     if entries is None:
         entries = load()
     if device_name is None:
@@ -179,7 +181,8 @@ def apply(entries=None, device_name=None, setter=None):
         if e["device"] != device_name:
             continue
         setter(e["n"], e["alpha"], e["c"], e["precision"],
-               [{f: g[f] for f in ("ylo", "yhi", "kind", "threads")} for g in e["groups"]])
+               [{f: g[f] for f in ("ylo", "yhi", "kind", "threads")} for g in e["groups"]
+                if (g["kind"], g["threads"]) != (g.get("default_kind"), g.get("default_threads"))])
         k += 1
     return k
 

@@ -35,9 +35,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_struct_sizes(lib):
-    assert lib.gmine_abi_version() == 2
+    assert lib.gmine_abi_version() == 3
     assert gmine.SCORE_DTYPE.itemsize == 72
-    assert ctypes.sizeof(gmine.Trace) == 112
+    assert ctypes.sizeof(gmine.Trace) == 120
     assert ctypes.sizeof(gmine.DPChoice) == 24
 
 
@@ -59,7 +59,7 @@ def test_B_and_cells_agree_with_oracle(lib):
 
 
 def test_strerror_texts(lib):
-    for s in range(0, 10):
+    for s in range(0, 11):
         assert isinstance(gmine.strerror(s), str) and gmine.strerror(s)
     assert "unknown" in gmine.strerror(12345)
 

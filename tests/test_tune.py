@@ -92,6 +92,12 @@ def test_cache_merge_and_apply_per_device(tmp_path):
     assert [(g["kind"], g["threads"]) for g in ch] == [(gmine.DP_MID, 256), (gmine.DP_WARP, 64)]
     assert tune.apply(entries, device_name="absent", setter=lambda *a: calls.append(a)) == 0
     assert tune.load(str(tmp_path / "none.json")) == []
+    # a group whose best was the planner's own choice stays with the rules
+    e3 = dict(e1, device="third-gpu", groups=[dict(e1["groups"][0]), dict(e1["groups"][1])])
+    e3["groups"][0].update(kind=e3["groups"][0]["default_kind"], threads=e3["groups"][0]["default_threads"])
+    calls.clear()
+    assert tune.apply([e3], device_name="third-gpu", setter=lambda *a: calls.append(a)) == 1
+    assert [(g["kind"], g["threads"]) for g in calls[0][4]] == [(gmine.DP_WARP, 64)]
 
 
 @pytest.mark.gpu
