@@ -18,8 +18,61 @@
 
 namespace gm {
 
+// samples per lane whose loads a per-sample loop issues together
+constexpr int kBatch = 4;
+
 __device__ __forceinline__ bool bit_of(const uint32_t* bm, int g) {
   return (bm[g >> 5] >> (g & 31)) & 1u;
+}
+
+// EquipartitionYAxis over the clumps (cstart[g] = P_g, the first position
+// of clump g; cstart[nc] = n): with the current row (superclump) number
+// `row` starting at position R0, the next one starts at the first clump g
+// after the current row's first clump with
+//   (P_g + P_{g+1} - 2 R0) (khat - row + 1) >= 2 (n - R0),
+// the exact integer form of 2# + |S| >= 2d; the left side grows with g.  If
+// there is none, the rest of the clumps form the last row.  Writes the row
+// starts scb[0..rows-1] and scb[rows] = n and returns rows.
+template <bool WIDE>
+__device__ __forceinline__ bool row_ends_at(int Sg, int R0, int mult, int rhs) {
+  if constexpr (WIDE) return (long long)(Sg - 2 * R0) * mult >= rhs;
+  else return (Sg - 2 * R0) * mult >= rhs;
+}
+
+// The warp tests 32 clumps per ballot and takes the first.
+template <bool WIDE, typename IT>
+__device__ int superclump_rows_warp(const IT* __restrict__ cstart, int nc, int n, int khat,
+                                    IT* __restrict__ scb, int lane) {
+  int R0 = 0, g0 = 0, row = 1;
+  if (lane == 0) scb[0] = 0;
+  for (;;) {
+    const int mult = khat - row + 1;
+    const int rhs = 2 * (n - R0);
+    int found = -1, Pf = 0;
+    for (int gb = g0 + 1; gb < nc; gb += 32) {
+      const int g = gb + lane;
+      int Pg = 0;
+      bool ok = false;
+      if (g < nc) {
+        Pg = cstart[g];
+        ok = row_ends_at<WIDE>(Pg + (int)cstart[g + 1], R0, mult, rhs);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (m) {
+        const int src = __ffs(m) - 1;
+        found = gb + src;
+        Pf = __shfl_sync(0xffffffffu, Pg, src);
+        break;
+      }
+    }
+    if (found < 0) break;  // the rest of the clumps form the last row
+    R0 = Pf;
+    g0 = found;
+    if (lane == 0) scb[row] = (IT)R0;
+    ++row;
+  }
+  if (lane == 0) scb[row] = (IT)n;
+  return row;
 }
 
 template <bool GLOBAL, typename IT>
@@ -111,17 +164,28 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       if (ties)
         for (int w = lane; w < (GU + 31) / 32; w += 32) mixed[w] = 0u;
       __syncwarp();
-      // rows of the V-sorted positions (each lane's row only moves forward;
+      // rows of the V-sorted positions (row r holds [eb[r], eb[r+1]);
       // eb[yhat] = n), then of the U-sorted positions
-      {
-        int r = 0;
-        for (int p = lane; p < n; p += 32) {
-          while (eb[r + 1] <= p) ++r;
-          Qs[p] = (IT)r;
-        }
+      for (int r = 0; r < yhat; ++r) {
+        const int b1 = eb[r + 1];
+#pragma unroll 4
+        for (int p = eb[r] + lane; p < b1; p += 32) Qs[p] = (IT)r;
       }
       __syncwarp();
-      for (int m = lane; m < n; m += 32) q[m] = Qs[pi[m]];
+      // (the loops over samples take kBatch of a lane's samples at a time,
+      // loads first: the stores into the same shared memory would otherwise
+      // keep the next sample's loads from starting early)
+      for (int m0 = lane; m0 < n; m0 += 32 * kBatch) {
+        int pv[kBatch];
+        IT qv[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) pv[u] = m0 + 32 * u < n ? (int)pi[m0 + 32 * u] : 0;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) qv[u] = Qs[pv[u]];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+          if (m0 + 32 * u < n) q[m0 + 32 * u] = qv[u];
+      }
       __syncwarp();
       // x-tie runs whose rows are mixed get one fresh label (Algorithm
       // GetClumpsPartition, first pass; one label per run)
@@ -133,28 +197,36 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       __syncwarp();
       // a clump starts where the label changes (second pass): ballot per 32
       int nc = 0;
-      for (int base = 0; base < n; base += 32) {
-        const int m = base + lane;
-        bool f = false;
-        if (m < n) {
-          if (m == 0) {
-            f = true;
-          } else {
-            if (ties) {
-              const int g = gU[m], gp = gU[m - 1];
-              f = g != gp && (bit_of(mixed, g) || bit_of(mixed, gp) || q[m] != q[m - 1]);
+      for (int base = 0; base < n; base += 32 * kBatch) {
+        bool f[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int m = base + 32 * u + lane;
+          f[u] = false;
+          if (m < n) {
+            if (m == 0) {
+              f[u] = true;
             } else {
-              f = q[m] != q[m - 1];
+              if (ties) {
+                const int g = gU[m], gp = gU[m - 1];
+                f[u] = g != gp && (bit_of(mixed, g) || bit_of(mixed, gp) || q[m] != q[m - 1]);
+              } else {
+                f[u] = q[m] != q[m - 1];
+              }
             }
           }
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, f);
-        const int before = __popc(mask & ((1u << lane) - 1u));
-        if (m < n) {
-          cgrp[m] = (IT)(nc + before + (f ? 1 : 0) - 1);
-          if (f) cstart[nc + before] = (IT)m;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int m = base + 32 * u + lane;
+          const unsigned mask = __ballot_sync(0xffffffffu, f[u]);
+          const int before = __popc(mask & ((1u << lane) - 1u));
+          if (m < n) {
+            cgrp[m] = (IT)(nc + before + (f[u] ? 1 : 0) - 1);
+            if (f[u]) cstart[nc + before] = (IT)m;
+          }
+          nc += __popc(mask);
         }
-        nc += __popc(mask);
       }
       if (lane == 0) cstart[nc] = (IT)n;
       __syncwarp();
@@ -164,42 +236,11 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       int k;
       const bool superclump = nc > khat;
       if (superclump) {
-        // EquipartitionYAxis over the clumps (cstart[g] = P_g, cstart[nc] =
-        // n): with the current superclump starting at position R0 = P_g0 and
-        // being number `row`, the next one starts at the first clump g > g0
-        // with (P_g + P_{g+1} - 2 R0) (khat - row + 1) >= 2 (n - R0) (the
-        // exact integer form of 2# + |S| >= 2d); the left side grows with g,
-        // so the warp tests 32 clumps at a time and takes the first by ballot
-        int R0 = 0, g0 = 0, row = 1;
-        if (lane == 0) scb[0] = 0;
-        for (;;) {
-          const int mult = khat - row + 1;
-          const int rhs = 2 * (n - R0);
-          int found = -1, Pf = 0;
-          for (int gb = g0 + 1; gb < nc; gb += 32) {
-            const int g = gb + lane;
-            int Pg = 0;
-            bool ok = false;
-            if (g < nc) {
-              Pg = cstart[g];
-              ok = (Pg + (int)cstart[g + 1] - 2 * R0) * mult >= rhs;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (m) {
-              const int src = __ffs(m) - 1;
-              found = gb + src;
-              Pf = __shfl_sync(0xffffffffu, Pg, src);
-              break;
-            }
-          }
-          if (found < 0) break;  // the rest of the clumps form the last row
-          R0 = Pf;
-          g0 = found;
-          if (lane == 0) scb[row] = (IT)R0;
-          ++row;
-        }
-        if (lane == 0) scb[row] = (IT)n;
-        k = row;
+        // (the products reach (2n) * khat: 64-bit where that passes 2^31)
+        const int rows = 2LL * n * khat >= (1LL << 31)
+                             ? superclump_rows_warp<true>(cstart, nc, n, khat, scb, lane)
+                             : superclump_rows_warp<false>(cstart, nc, n, khat, scb, lane);
+        k = rows;
       } else {
         for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
         k = nc;
@@ -220,14 +261,25 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       for (int i = lane; i < (yhat * ks + per_word - 1) / per_word; i += 32)
         reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
       __syncwarp();
-      for (int m = lane; m < n; m += 32) {
-        const int c = cgrp[m];
-        const int t = superclump ? (int)sc_of[c] : c;
-        const int i = (int)q[m] * ks + t + 1;
-        if constexpr (sizeof(IT) == 2)
-          atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (i >> 1), 1u << (16 * (i & 1)));
-        else
-          atomicAdd(reinterpret_cast<uint32_t*>(cnt) + i, 1u);
+      for (int m0 = lane; m0 < n; m0 += 32 * kBatch) {
+        int ci[kBatch], ti[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const bool in = m0 + 32 * u < n;
+          ci[u] = in ? (int)cgrp[m0 + 32 * u] : 0;
+          ti[u] = in ? (int)q[m0 + 32 * u] : -1;  // row, -1 past the end
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) ci[u] = superclump ? (int)sc_of[ci[u]] : ci[u];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          if (ti[u] < 0) continue;
+          const int i = ti[u] * ks + ci[u] + 1;
+          if constexpr (sizeof(IT) == 2)
+            atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (i >> 1), 1u << (16 * (i & 1)));
+          else
+            atomicAdd(reinterpret_cast<uint32_t*>(cnt) + i, 1u);
+        }
       }
       __syncwarp();
       // prefix over superclumps, written to the record; row totals give H(Q)
