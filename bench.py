@@ -41,9 +41,9 @@ L2_FLUSH_BYTES = 256 << 20
 FP64_PER_SM_CLK = 2
 # DRAM bytes (read + write) per DP task of the float DP launches, from the
 # ncu launch list of the 60-variable case (profiles/launches_config3_60vars.md:
-# 1,200 MB for 254,880 tasks); the launches read their task records and
+# 1,160 MB for 254,880 tasks); the launches read their task records and
 # little else, so the traffic scales with the tasks
-DP_DRAM_BYTES_PER_TASK = 4.7e3
+DP_DRAM_BYTES_PER_TASK = 4.55e3
 
 
 def parse():

@@ -16,7 +16,7 @@ using namespace gm;
 
 namespace {
 
-constexpr int64_t kChunkPairs = 32768;  // largest chunk of pairs per pass
+constexpr int64_t kChunkPairs = 65536;  // largest chunk of pairs per pass
 constexpr int kRankThreads = 1024;
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
@@ -285,7 +285,7 @@ MidPlan make_mid_plan(int n, const TaskBounds& tb, bool fp32, int threads) {
 
 constexpr int kDPThreadsBig = 256;
 constexpr int kDPThreadsSmall = 128;
-constexpr int64_t kRecBudget = 3LL << 30;  // record bytes per chunk
+constexpr int64_t kRecBudget = 12LL << 30;  // record bytes per chunk
 constexpr int kMaxDPGroups = 16;
 
 // One launch of the DP kernel: the tasks with row counts y in [ylo, yhi],
