@@ -292,7 +292,8 @@ __device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const 
 
 // The work for block b+1 (t in [t1, t1 + 32)) while warp 0 solves block b,
 // in items from one shared counter, LEV levels per pass:
-//   A1 s-chunks of 32, s in [1, t0) (rows final before block b);
+//   A1 s-chunks of 64 (32 below 24 levels per pass), s in [1, t0) (rows
+//   final before block b);
 //   block b+1's in-block triangle, 32 entries per item, into EbN (a buffer
 //   of its own, or, with eb_wait, block b's once warp 0 holds that in
 //   registers: *ebfree >= want);
@@ -313,7 +314,8 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
   constexpr int nT = (kEbEntries + 31) / 32;
   const int nlev = lmax - 1;
   const int npass = (nlev + LEV - 1) / LEV;
-  const int nsb1 = (t0 - 1 + 31) / 32;
+  constexpr int CH1 = LEV >= 24 ? 64 : 32;  // s per A1 item
+  const int nsb1 = (t0 - 1 + CH1 - 1) / CH1;
   const int nA1 = npass * nsb1;
   const int n2 = min(NW, 8);  // A2 items per pass
   const int ch2 = 32 / n2;
@@ -334,8 +336,8 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
     int pass, s_lo, s_hi;
     if (g < nA1) {
       pass = g / nsb1;
-      s_lo = 1 + (g - pass * nsb1) * 32;
-      s_hi = min(t0 - 1, s_lo + 31);
+      s_lo = 1 + (g - pass * nsb1) * CH1;
+      s_hi = min(t0 - 1, s_lo + CH1 - 1);
     } else if (g < nA1 + nT) {
       if (eb_wait && !waited_eb) {
         wait_ready(ebfree, want, lane, late);

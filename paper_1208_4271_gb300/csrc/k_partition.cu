@@ -39,6 +39,38 @@ __device__ __forceinline__ bool row_ends_at(int Sg, int R0, int mult, int rhs) {
   else return (Sg - 2 * R0) * mult >= rhs;
 }
 
+// One thread, clump after clump, the clump starts loaded eight at a time
+// ahead of the tests: for few clumps per row, where the warp's per-row
+// ballot, find-first and shuffle would cost more than a compare per clump.
+template <bool WIDE, typename IT>
+__device__ int superclump_rows_seq(const IT* __restrict__ cstart, int nc, int n, int khat,
+                                   IT* __restrict__ scb) {
+  constexpr int kAhead = 8;
+  int R0 = 0, row = 1;
+  scb[0] = 0;
+  int mult = khat, rhs = 2 * n;
+  int Pg = cstart[1];
+  for (int g = 1; g < nc; g += kAhead) {
+    int Pn[kAhead];
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) Pn[j] = g + 1 + j <= nc ? (int)cstart[g + 1 + j] : n;
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) {
+      const int Pj = j == 0 ? Pg : Pn[j - 1];
+      if (g + j < nc && row_ends_at<WIDE>(Pj + Pn[j], R0, mult, rhs)) {
+        R0 = Pj;
+        scb[row] = (IT)R0;
+        ++row;
+        mult = khat - row + 1;
+        rhs = 2 * (n - R0);
+      }
+    }
+    Pg = Pn[kAhead - 1];
+  }
+  scb[row] = (IT)n;
+  return row;
+}
+
 // The warp tests 32 clumps per ballot and takes the first.
 template <bool WIDE, typename IT>
 __device__ int superclump_rows_warp(const IT* __restrict__ cstart, int nc, int n, int khat,
@@ -237,9 +269,17 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       const bool superclump = nc > khat;
       if (superclump) {
         // (the products reach (2n) * khat: 64-bit where that passes 2^31)
-        const int rows = 2LL * n * khat >= (1LL << 31)
-                             ? superclump_rows_warp<true>(cstart, nc, n, khat, scb, lane)
-                             : superclump_rows_warp<false>(cstart, nc, n, khat, scb, lane);
+        const bool wide = 2LL * n * khat >= (1LL << 31);
+        int rows;
+        if (nc <= 4 * khat) {  // (y = 2..4 at n = 1340, B = 75, c = 15)
+          int r1 = 0;
+          if (lane == 0) r1 = wide ? superclump_rows_seq<true>(cstart, nc, n, khat, scb)
+                                   : superclump_rows_seq<false>(cstart, nc, n, khat, scb);
+          rows = __shfl_sync(0xffffffffu, r1, 0);
+        } else {
+          rows = wide ? superclump_rows_warp<true>(cstart, nc, n, khat, scb, lane)
+                      : superclump_rows_warp<false>(cstart, nc, n, khat, scb, lane);
+        }
         k = rows;
       } else {
         for (int j = lane; j <= nc; j += 32) scb[j] = cstart[j];
