@@ -292,8 +292,7 @@ __device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const 
 
 // The work for block b+1 (t in [t1, t1 + 32)) while warp 0 solves block b,
 // in items from one shared counter, LEV levels per pass:
-//   A1 s-chunks of 64 (32 below 24 levels per pass), s in [1, t0) (rows
-//   final before block b);
+//   A1 s-chunks of CH1, s in [1, t0) (rows final before block b);
 //   block b+1's in-block triangle, 32 entries per item, into EbN (a buffer
 //   of its own, or, with eb_wait, block b's once warp 0 holds that in
 //   registers: *ebfree >= want);
@@ -314,7 +313,9 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
   constexpr int nT = (kEbEntries + 31) / 32;
   const int nlev = lmax - 1;
   const int npass = (nlev + LEV - 1) / LEV;
-  constexpr int CH1 = LEV >= 24 ? 64 : 32;  // s per A1 item
+  // s per A1 item (measured: 64 for the float instances of 24 levels and
+  // more, 32 below; 16 on the double path, whose passes split the levels)
+  constexpr int CH1 = !fp32 ? 16 : LEV >= 24 ? 64 : 32;
   const int nsb1 = (t0 - 1 + CH1 - 1) / CH1;
   const int nA1 = npass * nsb1;
   const int n2 = min(NW, 8);  // A2 items per pass

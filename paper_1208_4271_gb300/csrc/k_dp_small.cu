@@ -207,11 +207,29 @@ __global__ void __launch_bounds__(128) k_dp_small(DPParams P, SmallPlan S) {
           real best = NINF;
           int arg = l - 1;
           const int s_hi = min(t0 + 31, k);  // the warp's bound: s < the largest t
-          for (int s = l - 1; s < s_hi; ++s) {
-            const real v = W[s * LW + (l - 1)] - Et[tri_row(s, k) + tt - s - 1];
-            if (s < t && gt_neg(v, best)) {
-              best = v;
-              arg = s;
+          if constexpr (fp32) {
+            // E(s, tt) at tri_row(s, k) + tt - s - 1, which grows by k - s - 1
+            // from s to s + 1; W(s, l-1) a row further (measured: -4 % on the
+            // float launches, +1 % on the double ones, which keep the plain form)
+            int eo = tri_row(l - 1, k) + tt - l;
+            const real* wp = W + (l - 1) * LW + (l - 1);
+#pragma unroll 4
+            for (int s = l - 1; s < s_hi; ++s) {
+              const real v = *wp - Et[eo];
+              if (s < t && gt_neg(v, best)) {
+                best = v;
+                arg = s;
+              }
+              eo += k - s - 1;
+              wp += LW;
+            }
+          } else {
+            for (int s = l - 1; s < s_hi; ++s) {
+              const real v = W[s * LW + (l - 1)] - Et[tri_row(s, k) + tt - s - 1];
+              if (s < t && gt_neg(v, best)) {
+                best = v;
+                arg = s;
+              }
             }
           }
           if (t <= k) {

@@ -333,7 +333,18 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
         for (int r = lane; r < yhat; r += 32) {
           IT* row = cnt + r * ks;
           int run = 0;
-          for (int t = 0; t < ks; ++t) {
+          int t = 0;
+          for (; t + kBatch <= ks; t += kBatch) {  // the loads ahead of the stores
+            int a[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) a[u] = row[t + u];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+              run += a[u];
+              row[t + u] = (IT)run;
+            }
+          }
+          for (; t < ks; ++t) {
             run += row[t];
             row[t] = (IT)run;
           }
@@ -349,17 +360,29 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
       } else
       for (int r = 0; r < yhat; ++r) {
         int carry = 0;
-        for (int base = 0; base < ks; base += 32) {
-          const int i = base + lane;
-          const int v = i < ks ? cnt[r * ks + i] : 0;
-          int incl = v;
+        // kBatch chunks of 32 scanned side by side, then stored with the
+        // carry in order
+        for (int base = 0; base < ks; base += 32 * kBatch) {
+          int incl[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int i = base + 32 * u + lane;
+            incl[u] = i < ks ? (int)cnt[r * ks + i] : 0;
+          }
 #pragma unroll
           for (int d = 1; d < 32; d <<= 1) {
-            const int oo = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += oo;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+              const int oo = __shfl_up_sync(0xffffffffu, incl[u], d);
+              if (lane >= d) incl[u] += oo;
+            }
           }
-          if (i < ks) rcum[r * ks + i] = carry + incl;
-          carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int i = base + 32 * u + lane;
+            if (i < ks) rcum[r * ks + i] = carry + incl[u];
+            carry += __shfl_sync(0xffffffffu, incl[u], 31);
+          }
         }
         sL += P.L64[carry];  // increasing r, as H(Q) is defined
       }
