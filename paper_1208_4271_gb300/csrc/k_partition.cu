@@ -71,7 +71,8 @@ __device__ int superclump_rows_seq(const IT* __restrict__ cstart, int nc, int n,
   return row;
 }
 
-// The warp tests 32 clumps per ballot and takes the first.
+// The warp tests 32 clumps at a time; two warp-wide minimum reductions give
+// every lane the first hit and its start.
 template <bool WIDE, typename IT>
 __device__ int superclump_rows_warp(const IT* __restrict__ cstart, int nc, int n, int khat,
                                     IT* __restrict__ scb, int lane) {
@@ -89,11 +90,13 @@ __device__ int superclump_rows_warp(const IT* __restrict__ cstart, int nc, int n
         Pg = cstart[g];
         ok = row_ends_at<WIDE>(Pg + (int)cstart[g + 1], R0, mult, rhs);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (m) {
-        const int src = __ffs(m) - 1;
-        found = gb + src;
-        Pf = __shfl_sync(0xffffffffu, Pg, src);
+      // the first clump that ends the row, and its start (the starts grow
+      // with g, so the smallest start among the hits is the first one's)
+      const unsigned fg = __reduce_min_sync(0xffffffffu, ok ? (unsigned)g : 0xffffffffu);
+      const unsigned fp = __reduce_min_sync(0xffffffffu, ok ? (unsigned)Pg : 0xffffffffu);
+      if (fg != 0xffffffffu) {
+        found = (int)fg;
+        Pf = (int)fp;
         break;
       }
     }
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(128) k_partition_t(PartParams P) {
         // (the products reach (2n) * khat: 64-bit where that passes 2^31)
         const bool wide = 2LL * n * khat >= (1LL << 31);
         int rows;
-        if (nc <= 4 * khat) {  // (y = 2..4 at n = 1340, B = 75, c = 15)
+        if (nc <= 3 * khat) {  // (y = 2..3 at n = 1340, B = 75, c = 15)
           int r1 = 0;
           if (lane == 0) r1 = wide ? superclump_rows_seq<true>(cstart, nc, n, khat, scb)
                                    : superclump_rows_seq<false>(cstart, nc, n, khat, scb);
