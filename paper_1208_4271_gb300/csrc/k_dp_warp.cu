@@ -180,10 +180,36 @@ __global__ void __launch_bounds__(224, 2) k_dp_warp(DPParams P, WarpPlan S) {
           }
         }
         // ---- B: s inside the block
+        // the in-block column E(t0+i, t0+lane), i < lane, in registers.
+        // Lane j < 16 pairs with lane 31 - j (31 entries between them): in
+        // step q < 16 the high lane forms its own entry i = q, the low lane
+        // its own entry i = q while q < j and, for q > j, its partner's entry
+        // i = 31 - q, which a shuffle moves into the partner's ec[31 - q]:
+        // sixteen entropy terms per lane instead of thirty-one.
         float ec[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          ec[i] = (tv && i < lane) ? entropy_w<TDW>(Lt, sd, SW, yhat, td, t0 + i) : PINF;
+        for (int i = 0; i < 32; ++i) ec[i] = PINF;
+        {
+          const bool low = lane < 16;
+          const int tp = t0 + 31 - lane;  // the partner's t (for low lanes)
+          const bool pv = low && tp <= k;
+          int tdp[TDW];
+#pragma unroll
+          for (int c = 0; c < TDW; ++c) tdp[c] = (pv && c < SW) ? sd[tp * SW + c] : 0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const bool own = tv && q < lane;
+            const bool part = pv && q > lane;
+            int row[TDW];
+#pragma unroll
+            for (int c = 0; c < TDW; ++c) row[c] = own ? td[c] : tdp[c];
+            float v = PINF;
+            if (own || part) v = entropy_w<TDW>(Lt, sd, SW, yhat, row, own ? t0 + q : t0 + 31 - q);
+            if (own) ec[q] = v;
+            const float recv = __shfl_sync(0xffffffffu, v, 31 - lane);
+            if (!low && tv && 31 - q < lane) ec[31 - q] = recv;
+          }
+        }
         float rcur = tv ? Rt[t * LS] : NINF;  // level 1
 #pragma unroll
         for (int li = 0; li < LEV; ++li) {
