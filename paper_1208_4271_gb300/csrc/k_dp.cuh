@@ -168,11 +168,20 @@ __device__ __forceinline__ unsigned long long splat_x2(float e) {
 // next iteration is formed meanwhile.
 // REG: 4 or 8 = row t in registers, that many columns; 1 = row t in
 // registers, yhat terms; 0 = both rows from shared memory.
-template <typename real, int LEV, int REG>
+// Prefetch into L1 of the line holding p (a hint: no fault, no result).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Rows ahead of the current s whose R lines are prefetched when the R table
+// is in global memory.
+constexpr int kPfRows = 8;
+
+template <typename real, int LEV, int REG, bool PF>
 __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
                                            int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
                                            const int* __restrict__ sd, int SW, int yhat,
-                                           const int (&td)[8], int tt) {
+                                           const int (&td)[8], int tt, bool sdg = false) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   auto E = [&](int s) -> real {
@@ -185,6 +194,20 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
     real e0 = E(s), e1 = E(s + 1);
 #pragma unroll 1
     for (; s + 1 <= s_hi; s += 2) {
+      if constexpr (PF) {
+        // the R rows (global memory) kPfRows ahead into L1: the loads of
+        // this iteration are then L1 hits, not trips to L2 or DRAM
+        if (s + kPfRows + 1 <= s_hi) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const char* p0 = reinterpret_cast<const char*>(Rt + (s + kPfRows + r) * LS + (lc - 2));
+#pragma unroll
+            for (int b = 0; b < LEV * (int)sizeof(real) + 127; b += 128) prefetch_l1(p0 + b);
+          }
+          // the superclump rows too when they are in global memory
+          if (sdg) prefetch_l1(sd + (s + kPfRows) * SW);
+        }
+      }
       const bool more = s + 3 <= s_hi;
       const real n0 = more ? E(s + 2) : e0;
       const real n1 = more ? E(s + 3) : e1;
@@ -300,14 +323,15 @@ __device__ __forceinline__ void in_block_entropies(real* __restrict__ Eb, const 
 //   until warp 0 has published block b's rows (*ready >= want).
 // The A items of a pass share the running maxima, flushed into the X rows of
 // block b+1 by atomicMin on the value bits when the pass changes.
-template <typename real, int LEV>
+template <typename real, int LEV, bool RSM>
 __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS, int lmax, int t0,
                                             int t1, int k, int* cnt, const int* ready,
                                             const int* ebfree, int want,
                                             const real* __restrict__ Lt, const int* __restrict__ sd,
                                             int SW, int yhat, int tt, bool tv,
                                             typename Bits<real>::U* Xrow, real* __restrict__ EbN,
-                                            bool eb_wait, int NW, int lane, bool& late) {
+                                            bool eb_wait, int NW, int lane, bool& late,
+                                            bool sdg) {
   using BT = Bits<real>;
   constexpr bool fp32 = sizeof(real) == 4;
   constexpr int nT = (kEbEntries + 31) / 32;
@@ -370,13 +394,17 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
     // float: the row width's fixed number of terms, no branch on yhat; double:
     // only yhat terms (the padding terms would cost FP64 issue slots)
     if (reg && fp32 && SW == 4)
-      accumulate<real, LEV, 4>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+      accumulate<real, LEV, 4, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
+                                       sdg);
     else if (reg && fp32)
-      accumulate<real, LEV, 8>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+      accumulate<real, LEV, 8, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
+                                       sdg);
     else if (reg)
-      accumulate<real, LEV, 1>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+      accumulate<real, LEV, 1, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
+                                       sdg);
     else
-      accumulate<real, LEV, 0>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+      accumulate<real, LEV, 0, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
+                                       sdg);
   }
   if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
 }
@@ -407,7 +435,7 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
                                               const typename Bits<real>::U* __restrict__ Xcur,
                                               bool has_x, const real* __restrict__ Eb,
                                               real* __restrict__ rbuf, int lane,
-                                              int* ebfree, int eb_val) {
+                                              int* ebfree, int eb_val, bool xg = false) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   const int t = t0 + lane;
@@ -435,6 +463,8 @@ __device__ __forceinline__ void phase_b_level(real* __restrict__ Rt, real* __res
     real* rb = rbuf + par * 32;
     // the partial maximum from the earlier blocks does not depend on the
     // chain: read it before the broadcast
+    // (X rows in global memory: the lane's next 32 levels into L1)
+    if (xg && ((l - 2) & 31) == 0) prefetch_l1(xr + l + 31);
     const real xl = has_x ? BT::from(xr[l - 1]) : BT::ninf();
     rb[lane] = rcur;
     __syncwarp();
@@ -616,7 +646,7 @@ k_dp(DPParams P, DPPlan S) {
         if (warp == 0) {
           // ---- block b, s inside the block
           phase_b_level<real>(Rt, Rtop, LS, LX, lmax, t0, k, Xcur, b > 0, (b & 1) ? Eb2 : Eb, rbuf,
-                              lane, Eb2 == Eb ? &s_ebfree : nullptr, b + 1);
+                              lane, Eb2 == Eb ? &s_ebfree : nullptr, b + 1, !RSM && S.off_X < 0 && b > 0);
           // block b's X rows are consumed: cleared for block b+2; the other
           // counter is free until the next step
           for (int i = lane; i < 32 * LX; i += 32) Xcur[i] = NINF_BITS;
@@ -632,9 +662,10 @@ k_dp(DPParams P, DPPlan S) {
         if (next) {
           const int tn = t1 + lane;  // this lane's t in block b+1
           const bool tnv = tn <= k;
-          block_items<real, LEV>(Rt, LS, lmax, t0, t1, k, &s_cnt[b & 1], &s_ready, &s_ebfree, b + 1,
+          block_items<real, LEV, RSM>(Rt, LS, lmax, t0, t1, k, &s_cnt[b & 1], &s_ready, &s_ebfree, b + 1,
                                  Lt, sd, SW, yhat, tnv ? tn : k, tnv, Xnxt + lane * LX,
-                                 ((b + 1) & 1) ? Eb2 : Eb, Eb2 == Eb, NW, lane, late);
+                                 ((b + 1) & 1) ? Eb2 : Eb, Eb2 == Eb, NW, lane, late,
+                                 !RSM && S.off_sd < 0);
         }
         __syncthreads();
       }
