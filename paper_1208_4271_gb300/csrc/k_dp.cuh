@@ -161,13 +161,6 @@ __device__ __forceinline__ unsigned long long splat_x2(float e) {
   return v;
 }
 
-// Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels
-// l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.  Two s
-// per iteration: each level takes both candidates in one three-operand max
-// (in float two levels share one packed subtraction), and the E pair of the
-// next iteration is formed meanwhile.
-// REG: 4 or 8 = row t in registers, that many columns; 1 = row t in
-// registers, yhat terms; 0 = both rows from shared memory.
 // Prefetch into L1 of the line holding p (a hint: no fault, no result).
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -177,6 +170,15 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
 // is in global memory.
 constexpr int kPfRows = 8;
 
+// Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels
+// l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.  Two s
+// per iteration: each level takes both candidates in one three-operand max
+// (in float two levels share one packed subtraction), and the E pair of the
+// next iteration is formed meanwhile.
+// REG: 4 or 8 = row t in registers, that many columns; 1 = row t in
+// registers, yhat terms; 0 = both rows from shared memory.
+// PF: the R table is in global memory (its rows, and with sdg the
+// superclump rows, are prefetched into L1 kPfRows ahead).
 template <typename real, int LEV, int REG, bool PF>
 __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
                                            int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
