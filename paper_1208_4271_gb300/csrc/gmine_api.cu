@@ -144,7 +144,10 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   S.x_scr_off = -1;
   S.sd_scr_off = -1;
   S.cuts_scr_off = -1;
-  if (!in_smem && fixed + reserve > smem_optin) {
+  // (a global R table comes with phase A's staging buffers of R rows, one
+  // per warp, in shared memory)
+  const int64_t stage_b = (int64_t)NW * kDPStageBytes;
+  if (!in_smem && fixed + stage_b + reserve > smem_optin) {
     fixed = place(false, true);
     S.x_scr_off = scr;
     scr = align256(scr + xrows);
@@ -154,10 +157,10 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
     // float path that frees room for the L table beside two CTAs per SM
     // (each entropy term reads a row and yhat + 1 table entries: one of the two
     // stays in shared memory)
-    bool sd_out = fixed + reserve > smem_optin;
-    if (!sd_out && fp32 && 2 * (fixed + reserve) > smem_optin + 1024) {
+    bool sd_out = fixed + stage_b + reserve > smem_optin;
+    if (!sd_out && fp32 && 2 * (fixed + stage_b + reserve) > smem_optin + 1024) {
       const int64_t without = place(false, false);
-      sd_out = 2 * (((without + 15) & ~int64_t(15)) + lbytes + reserve) <= smem_optin + 1024;
+      sd_out = 2 * (((without + 15) & ~int64_t(15)) + stage_b + lbytes + reserve) <= smem_optin + 1024;
       place(false, true);
     }
     if (sd_out) {
@@ -168,6 +171,11 @@ DPPlan make_dp_plan(int n, const TaskBounds& tb, bool fp32, int threads, int sme
   }
   S.scr_bytes = in_smem ? 0 : scr;
   int64_t o = fixed;
+  S.off_stage = -1;
+  if (!in_smem) {
+    S.off_stage = (int)((o + 15) & ~int64_t(15));
+    o = (S.off_stage + stage_b + 15) & ~int64_t(15);
+  }
   if (in_smem) {
     S.off_L = (int)o;
     o = (o + lbytes + 15) & ~int64_t(15);

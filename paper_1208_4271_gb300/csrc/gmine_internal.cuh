@@ -244,6 +244,11 @@ struct PartParams {
   int64_t gscr_per_cta;
 };
 
+// Rows of the global R table a warp of the blocked DP stages in shared
+// memory at a time, and the bytes of its buffer (rows of up to 160 bytes).
+constexpr int kDPStageRows = 16;
+constexpr int kDPStageBytes = kDPStageRows * 160;
+
 struct DPParams {
   PairPrep pp;
   const int32_t* rec;
@@ -298,6 +303,7 @@ struct MidPlan {
 struct DPPlan {
   int off_R, off_Rtop, off_X, off_Eb, off_rbuf, off_L, off_sd;
   int off_Eb2;  // a second in-block triangle (double buffering), or -1
+  int off_stage;  // per-warp staging buffers of R rows (R table in global memory)
   int64_t sd_scr_off;  // off_sd < 0: the superclump rows live in the CTA's global scratch here
   int64_t x_scr_off;   // off_X < 0: the X buffers live in the CTA's global scratch here
   int off_tb;          // traceback scratch (cuts, I(l), l*(l)): the X region, or its own

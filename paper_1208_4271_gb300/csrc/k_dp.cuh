@@ -166,24 +166,26 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Rows ahead of the current s whose R lines are prefetched when the R table
-// is in global memory.
-constexpr int kPfRows = 8;
+// With the R table in global memory, phase A copies the rows of its s-range
+// into a per-warp shared-memory buffer kStageRows at a time (coalesced
+// 16-byte loads, the next rows prefetched into L1 meanwhile) and reads them
+// there as broadcasts; kDPStageBytes per warp hold kStageRows rows of up to
+// 160 bytes (40 float or 20 double levels per pass).
+constexpr int kStageRows = kDPStageRows;
 
-// Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels
-// l = lc .. lc+LEV-1 (R columns lc-2 ..), max-accumulated into acc.  Two s
-// per iteration: each level takes both candidates in one three-operand max
-// (in float two levels share one packed subtraction), and the E pair of the
-// next iteration is formed meanwhile.
+// Candidates R(s, l-1) - E(s, t) for s in [s_lo, s_hi] and the LEV levels of
+// one pass, max-accumulated into acc; row s of the pass's R columns starts at
+// Rb + (s - s_base) * RS.  Two s per iteration: each level takes both
+// candidates in one three-operand max (in float two levels share one packed
+// subtraction), and the E pair of the next iteration is formed meanwhile.
 // REG: 4 or 8 = row t in registers, that many columns; 1 = row t in
 // registers, yhat terms; 0 = both rows from shared memory.
-// PF: the R table is in global memory (its rows, and with sdg the
-// superclump rows, are prefetched into L1 kPfRows ahead).
-template <typename real, int LEV, int REG, bool PF>
-__device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
-                                           int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
-                                           const int* __restrict__ sd, int SW, int yhat,
-                                           const int (&td)[8], int tt, bool sdg = false) {
+template <typename real, int LEV, int REG>
+__device__ __forceinline__ void accumulate_rows(real (&acc)[LEV], const real* __restrict__ Rb, int RS,
+                                                int s_base, int s_lo, int s_hi,
+                                                const real* __restrict__ Lt,
+                                                const int* __restrict__ sd, int SW, int yhat,
+                                                const int (&td)[8], int tt) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
   auto E = [&](int s) -> real {
@@ -196,20 +198,79 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
     real e0 = E(s), e1 = E(s + 1);
 #pragma unroll 1
     for (; s + 1 <= s_hi; s += 2) {
-      if constexpr (PF) {
-        // the R rows (global memory) kPfRows ahead into L1: the loads of
-        // this iteration are then L1 hits, not trips to L2 or DRAM
-        if (s + kPfRows + 1 <= s_hi) {
+      const bool more = s + 3 <= s_hi;
+      const real n0 = more ? E(s + 2) : e0;
+      const real n1 = more ? E(s + 3) : e1;
+      const real* R0 = Rb + (s - s_base) * RS;
+      const real* R1 = R0 + RS;
+      unsigned long long ee0 = 0, ee1 = 0;
+      if constexpr (sizeof(real) == 4) {
+        ee0 = splat_x2(e0);
+        ee1 = splat_x2(e1);
+      }
 #pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const char* p0 = reinterpret_cast<const char*>(Rt + (s + kPfRows + r) * LS + (lc - 2));
-#pragma unroll
-            for (int b = 0; b < LEV * (int)sizeof(real) + 127; b += 128) prefetch_l1(p0 + b);
-          }
-          // the superclump rows too when they are in global memory
-          if (sdg) prefetch_l1(sd + (s + kPfRows) * SW);
+      for (int g = 0; g < LEV / VW; ++g) {
+        if constexpr (sizeof(real) == 4) {
+          // four levels of rows s and s+1, two subtractions per instruction
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(R0 + 4 * g);
+          const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(R1 + 4 * g);
+          const float2 a0 = sub_x2(a.x, ee0), a1 = sub_x2(a.y, ee0);
+          const float2 b0 = sub_x2(b.x, ee1), b1 = sub_x2(b.y, ee1);
+          acc[4 * g + 0] = fmax3(acc[4 * g + 0], a0.x, b0.x);
+          acc[4 * g + 1] = fmax3(acc[4 * g + 1], a0.y, b0.y);
+          acc[4 * g + 2] = fmax3(acc[4 * g + 2], a1.x, b1.x);
+          acc[4 * g + 3] = fmax3(acc[4 * g + 3], a1.y, b1.y);
+        } else {
+          const double2 a = *reinterpret_cast<const double2*>(R0 + 2 * g);
+          const double2 b = *reinterpret_cast<const double2*>(R1 + 2 * g);
+          acc[2 * g + 0] = fmax3(acc[2 * g + 0], a.x - e0, b.x - e1);
+          acc[2 * g + 1] = fmax3(acc[2 * g + 1], a.y - e0, b.y - e1);
         }
       }
+      e0 = n0;
+      e1 = n1;
+    }
+  }
+  if (s == s_hi) {  // an odd count: the last s alone
+    const real e = E(s);
+    const real* Rs = Rb + (s - s_base) * RS;
+#pragma unroll
+    for (int g = 0; g < LEV / VW; ++g) {
+      if constexpr (sizeof(real) == 4) {
+        const float4 r = *reinterpret_cast<const float4*>(Rs + 4 * g);
+        acc[4 * g + 0] = BT::max(acc[4 * g + 0], r.x - e);
+        acc[4 * g + 1] = BT::max(acc[4 * g + 1], r.y - e);
+        acc[4 * g + 2] = BT::max(acc[4 * g + 2], r.z - e);
+        acc[4 * g + 3] = BT::max(acc[4 * g + 3], r.w - e);
+      } else {
+        const double2 r = *reinterpret_cast<const double2*>(Rs + 2 * g);
+        acc[2 * g + 0] = BT::max(acc[2 * g + 0], r.x - e);
+        acc[2 * g + 1] = BT::max(acc[2 * g + 1], r.y - e);
+      }
+    }
+  }
+}
+
+// The same for R rows in shared memory, row s at Rt + s * LS + (lc - 2)
+// (a copy of its own: sharing accumulate_rows cost the y = 2 launch 2 %
+// through a different schedule).
+template <typename real, int LEV, int REG>
+__device__ __forceinline__ void accumulate_smem(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
+                                           int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
+                                           const int* __restrict__ sd, int SW, int yhat,
+                                           const int (&td)[8], int tt) {
+  using BT = Bits<real>;
+  constexpr int VW = 16 / sizeof(real);
+  auto E = [&](int s) -> real {
+    if constexpr (REG == 4 || REG == 8) return entropy_regc<real, REG>(Lt, sd, td, s);
+    else if constexpr (REG == 1) return entropy_reg<real>(Lt, sd, SW, yhat, td, s);
+    else return entropy_term<real>(Lt, sd, SW, yhat, s, tt);
+  };
+  int s = s_lo;
+  if (s < s_hi) {
+    real e0 = E(s), e1 = E(s + 1);
+#pragma unroll 1
+    for (; s + 1 <= s_hi; s += 2) {
       const bool more = s + 3 <= s_hi;
       const real n0 = more ? E(s + 2) : e0;
       const real n1 = more ? E(s + 3) : e1;
@@ -259,6 +320,53 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
         acc[2 * g + 0] = BT::max(acc[2 * g + 0], r.x - e);
         acc[2 * g + 1] = BT::max(acc[2 * g + 1], r.y - e);
       }
+    }
+  }
+}
+
+// Phase A over s in [s_lo, s_hi] for the levels from lc: straight from the
+// R table in shared memory, or (GS: the R table in global memory) through
+// the warp's staging buffer, kStageRows rows at a time, the next rows (and
+// with sdg their superclump rows) prefetched into L1 before each copy.
+template <typename real, int LEV, int REG, bool GS>
+__device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restrict__ Rt, int LS,
+                                           int lc, int s_lo, int s_hi, const real* __restrict__ Lt,
+                                           const int* __restrict__ sd, int SW, int yhat,
+                                           const int (&td)[8], int tt, real* __restrict__ stage,
+                                           int lane, bool sdg) {
+  if constexpr (!GS) {
+    accumulate_smem<real, LEV, REG>(acc, Rt, LS, lc, s_lo, s_hi, Lt, sd, SW, yhat, td, tt);
+  } else {
+    constexpr int VW = 16 / sizeof(real);
+    constexpr int UPR = LEV / VW;  // 16-byte units per row
+    static_assert(LEV * sizeof(real) <= 160, "a staged row holds at most 160 bytes");
+    for (int sb = s_lo; sb <= s_hi; sb += kStageRows) {
+      const int se = min(s_hi, sb + kStageRows - 1);
+      // the next rows into L1 while this copy and its candidates run
+      {
+        // two lanes per row (its three lines at most: first, middle, last byte)
+        const int sp = se + 1 + (lane >> 1);
+        if (sp <= s_hi) {
+          constexpr int RB = LEV * (int)sizeof(real);
+          const char* p0 = reinterpret_cast<const char*>(Rt + sp * LS + (lc - 2));
+          if (lane & 1) {
+            prefetch_l1(p0 + RB - 1);
+          } else {
+            prefetch_l1(p0);
+            prefetch_l1(p0 + RB / 2);
+            if (sdg) prefetch_l1(sd + sp * SW);
+          }
+        }
+      }
+      __syncwarp();  // the previous rows are read
+      const int units = (se - sb + 1) * UPR;
+      for (int i = lane; i < units; i += 32) {
+        const int r = i / UPR, u = i - r * UPR;
+        reinterpret_cast<uint4*>(stage)[i] =
+            *reinterpret_cast<const uint4*>(Rt + (sb + r) * LS + (lc - 2) + u * VW);
+      }
+      __syncwarp();
+      accumulate_rows<real, LEV, REG>(acc, stage, LEV, sb, sb, se, Lt, sd, SW, yhat, td, tt);
     }
   }
 }
@@ -333,7 +441,7 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
                                             int SW, int yhat, int tt, bool tv,
                                             typename Bits<real>::U* Xrow, real* __restrict__ EbN,
                                             bool eb_wait, int NW, int lane, bool& late,
-                                            bool sdg) {
+                                            bool sdg, real* __restrict__ stage) {
   using BT = Bits<real>;
   constexpr bool fp32 = sizeof(real) == 4;
   constexpr int nT = (kEbEntries + 31) / 32;
@@ -397,16 +505,16 @@ __device__ __forceinline__ void block_items(const real* __restrict__ Rt, int LS,
     // only yhat terms (the padding terms would cost FP64 issue slots)
     if (reg && fp32 && SW == 4)
       accumulate<real, LEV, 4, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
-                                       sdg);
+                                       stage, lane, sdg);
     else if (reg && fp32)
       accumulate<real, LEV, 8, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
-                                       sdg);
+                                       stage, lane, sdg);
     else if (reg)
       accumulate<real, LEV, 1, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
-                                       sdg);
+                                       stage, lane, sdg);
     else
       accumulate<real, LEV, 0, !RSM>(acc, Rt, LS, 2 + pass * LEV, s_lo, s_hi, Lt, sd, SW, yhat, td, tt,
-                                       sdg);
+                                       stage, lane, sdg);
   }
   if (cur_pass >= 0 && tv) flush<real, LEV>(acc, Xrow, 2 + cur_pass * LEV, lmax);
 }
@@ -545,6 +653,8 @@ k_dp(DPParams P, DPPlan S) {
   // registers, then block b+1's
   real* Eb = reinterpret_cast<real*>(sm + S.off_Eb);
   real* Eb2 = S.off_Eb2 >= 0 ? reinterpret_cast<real*>(sm + S.off_Eb2) : Eb;
+  // this warp's staging buffer of R rows (R table in global memory)
+  real* stage = RSM ? nullptr : reinterpret_cast<real*>(sm + S.off_stage + warp * kDPStageBytes);
   real* rbuf = reinterpret_cast<real*>(sm + S.off_rbuf);  // [2][32]
   // [kmax+1][SW]: shared memory, or (global R table, very large k) after
   // the R table in the CTA's scratch
@@ -667,7 +777,7 @@ k_dp(DPParams P, DPPlan S) {
           block_items<real, LEV, RSM>(Rt, LS, lmax, t0, t1, k, &s_cnt[b & 1], &s_ready, &s_ebfree, b + 1,
                                  Lt, sd, SW, yhat, tnv ? tn : k, tnv, Xnxt + lane * LX,
                                  ((b + 1) & 1) ? Eb2 : Eb, Eb2 == Eb, NW, lane, late,
-                                 !RSM && S.off_sd < 0);
+                                 !RSM && S.off_sd < 0, stage);
         }
         __syncthreads();
       }
