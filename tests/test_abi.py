@@ -41,6 +41,22 @@ def test_abi_version_and_struct_sizes(lib):
     assert ctypes.sizeof(gmine.DPChoice) == 24
 
 
+def test_header_constants_match_the_binding():
+    """The status codes and the stage indexes of include/gmine.h are the
+    ones the Python binding uses."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "gmine.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (GMINE_\w+) (\d+)", hdr)}
+    for name in ("OK", "E_PARAM", "E_TOO_FEW", "E_CONSTANT", "E_NOMEM", "E_ARG", "E_WORKSPACE", "E_CUDA",
+                 "E_LIMIT", "E_NODEVICE", "E_TIMEOUT"):
+        assert defs["GMINE_" + name] == getattr(gmine, name), name
+    assert defs["GMINE_N_STAGES"] == gmine.N_STAGES == len(gmine.STAGE_NAMES)
+    for i, stage in enumerate(gmine.STAGE_NAMES):
+        assert defs["GMINE_STAGE_" + stage.upper()] == i, stage
+    assert defs["GMINE_ABI_VERSION"] == 3
+
+
 def test_check_param_matches_documented_ranges(lib):
     assert gmine.check_param(0.6, 15.0) == gmine.OK
     assert gmine.check_param(1.0, 0.5) == gmine.OK
