@@ -245,9 +245,10 @@ struct PartParams {
 };
 
 // Rows of the global R table a warp of the blocked DP stages in shared
-// memory at a time, and the bytes of its buffer (rows of up to 160 bytes).
+// memory at a time, and the bytes of its buffer (R rows of up to 160 bytes,
+// then superclump rows of up to 32 bytes).
 constexpr int kDPStageRows = 16;
-constexpr int kDPStageBytes = kDPStageRows * 160;
+constexpr int kDPStageBytes = kDPStageRows * (160 + 32);
 
 struct DPParams {
   PairPrep pp;

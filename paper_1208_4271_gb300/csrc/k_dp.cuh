@@ -185,11 +185,13 @@ __device__ __forceinline__ void accumulate_rows(real (&acc)[LEV], const real* __
                                                 int s_base, int s_lo, int s_hi,
                                                 const real* __restrict__ Lt,
                                                 const int* __restrict__ sd, int SW, int yhat,
-                                                const int (&td)[8], int tt) {
+                                                const int (&td)[8], int tt,
+                                                const int* __restrict__ sdr, int sd_off) {
   using BT = Bits<real>;
   constexpr int VW = 16 / sizeof(real);
+  // (the short rows of s at sdr + (s - sd_off) * REG: sd itself, or staged)
   auto E = [&](int s) -> real {
-    if constexpr (REG == 4 || REG == 8) return entropy_regc<real, REG>(Lt, sd, td, s);
+    if constexpr (REG == 4 || REG == 8) return entropy_regc<real, REG>(Lt, sdr, td, s - sd_off);
     else if constexpr (REG == 1) return entropy_reg<real>(Lt, sd, SW, yhat, td, s);
     else return entropy_term<real>(Lt, sd, SW, yhat, s, tt);
   };
@@ -365,8 +367,19 @@ __device__ __forceinline__ void accumulate(real (&acc)[LEV], const real* __restr
         reinterpret_cast<uint4*>(stage)[i] =
             *reinterpret_cast<const uint4*>(Rt + (sb + r) * LS + (lc - 2) + u * VW);
       }
+      // short superclump rows in global memory: staged beside them
+      constexpr bool SDS = REG == 4 || REG == 8;
+      int* sds = reinterpret_cast<int*>(reinterpret_cast<char*>(stage) + kStageRows * 160);
+      if (SDS && sdg) {
+        const int su = (se - sb + 1) * (REG / 4);
+        for (int i = lane; i < su; i += 32)
+          reinterpret_cast<int4*>(sds)[i] = reinterpret_cast<const int4*>(sd + sb * REG)[i];
+      }
       __syncwarp();
-      accumulate_rows<real, LEV, REG>(acc, stage, LEV, sb, sb, se, Lt, sd, SW, yhat, td, tt);
+      if (SDS && sdg)
+        accumulate_rows<real, LEV, REG>(acc, stage, LEV, sb, sb, se, Lt, sd, SW, yhat, td, tt, sds, sb);
+      else
+        accumulate_rows<real, LEV, REG>(acc, stage, LEV, sb, sb, se, Lt, sd, SW, yhat, td, tt, sd, 0);
     }
   }
 }
